@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the row-wise decomposed M-D FFT on GB300.
+
+Workload (one "step"): forward + normalised inverse 3-D complex64 FFT of a
+batch of B = 8 distinct 256x256x256 volumes (seeded U[-1,1) re/im), P = 4096
+virtual processes, the planner's best transpose order.  Every volume is
+128 MiB, larger than the 126 MB L2, and the step walks through 8 of them, so
+no L2 flush is needed between steps.
+
+value = algorithmic bytes / device time, the algorithmic bytes of one
+transform being 2 * M * T * 8 (M fused passes, each reading and writing the
+array once; the transposes are inside the passes).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (under torchrun) every rank runs an independent replica on
+its own GPU (the path has no exchange step on one node's GPUs here); rank 0
+prints the line with the max time over ranks.  --impl reference times the CPU
+FP64 oracle on the host cores instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "M-D FFT GB/s & % HBM peak vs plain; served FFT/s, p50/p99 at stated error"
+SHAPE = (256, 256, 256)
+P_DEFAULT = 4096
+PROFILE = os.path.join(ROOT, "profiles", "fft_pass_256cubed_c64.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1302_6189_gb300", "csrc", f) for f in
+                  ("fft_pass.cuh", "pass_c64.cu")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--P", type=int, default=P_DEFAULT)
+    ap.add_argument("--no-extra", action="store_true", help="skip the per-order / complex128 table")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        with open(PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    kv = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256")):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha256") != kernel_hash():
+        return None
+    try:
+        return int(float(kv["traffic_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        sm = []
+        smax = None
+        power = []
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes(shape, elem):
+    T = 1
+    for n in shape:
+        T *= n
+    return 2 * len(shape) * T * elem, T
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+
+def oracle_fwd_inv_seconds(shape, reps, nthreads):
+    """Wall time of `reps` forward + inverse FP64 oracle transforms of one volume."""
+    import numpy as np
+
+    import oracle
+    import synth_inputs as si
+    x = si.uniform_complex(shape, si.SEEDS["cube256"])
+    y = np.empty_like(x)
+    times = []
+    for _ in range(reps):
+        np.copyto(y, x)
+        t0 = time.perf_counter()
+        oracle.fftn_inplace(y, -1, nthreads)
+        oracle.fftn_inplace(y, +1, nthreads)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline(shape, elem):
+    nthreads = len(os.sched_getaffinity(0))
+    reps = 2
+    times = oracle_fwd_inv_seconds(shape, reps, nthreads)
+    per_step, _ = algorithmic_bytes(shape, elem)
+    gbs = 2 * per_step * reps / sum(times) / 1e9
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"{reps} x (forward + inverse) of one {'x'.join(map(str, shape))} volume, FP64 oracle "
+                      f"(complex128) on {nthreads} host threads; bytes counted as for the complex64 GPU path",
+            "seconds": round(sum(times), 3)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    nthreads = len(os.sched_getaffinity(0))
+    per_transform, _ = algorithmic_bytes(SHAPE, 8)
+    # warm-up and timed steps; one step = forward + inverse of one volume (a
+    # bounded sample of the 8-volume step of the GPU arm)
+    oracle_fwd_inv_seconds(SHAPE, max(0, args.warmup), nthreads) if args.warmup else None
+    times = oracle_fwd_inv_seconds(SHAPE, args.steps, nthreads)
+    total = sum(times)
+    gbs = 2 * per_transform * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "3-D FFT 256x256x256 forward+inverse, oracle sample of 1 volume per step",
+                       "P": args.P, "parallelism": "host threads"},
+            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+                             "sample": "one 256^3 volume forward + inverse per step (FP64)"},
+            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth_inputs as si
+    from paper_1302_6189_gb300 import Plan, format_order, mdfft_order_search
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    shape, B, P = SHAPE, args.batch, args.P
+    elem = 8
+    per_transform, T = algorithmic_bytes(shape, elem)
+    order, total_amount = mdfft_order_search(shape, P, 0)
+    plan = Plan(shape, P, order, "c64")
+    comm = plan.comm_volume()
+
+    xs = [torch.from_numpy(si.uniform_complex(shape, si.SEEDS["cube256"] + i, np.complex64)).to(dev)
+          for i in range(B)]
+    ys = [torch.empty_like(xs[0]) for _ in range(B)]
+    zs = [torch.empty_like(xs[0]) for _ in range(B)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for i in range(B):
+            plan.exec(xs[i], ys[i], dir=-1)
+            plan.exec(ys[i], zs[i], dir=+1, normalize=True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    err = float((torch.linalg.vector_norm(zs[0] - xs[0]) / torch.linalg.vector_norm(xs[0])).item())
+
+    clocks = ClockSampler(local)
+    plan.set_timing(True)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    pass_ms, n_timed = plan.pass_times()
+    plan.set_timing(False)
+    ms_max = max_over_ranks(ms, world)
+
+    bytes_per_step = 2 * B * per_transform
+    value = world * args.steps * bytes_per_step / (ms_max * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    launch_bytes = 2 * T * elem  # one pass: read and write the array once
+    avg_launch_ms = sum(pass_ms) / len(pass_ms)
+    achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
+    traffic = profile_traffic()
+
+    # end to end: host (pinned) buffers through mdfft_exec_host, copies inside the timed region
+    hx = [xs[i].cpu().pin_memory() for i in range(B)]
+    hy = [torch.empty_like(hx[0]).pin_memory() for _ in range(B)]
+    hz = [torch.empty_like(hx[0]).pin_memory() for _ in range(B)]
+    din, dout = torch.empty_like(xs[0]), torch.empty_like(xs[0])
+
+    def e2e_step():
+        for i in range(B):
+            plan.exec_host(hx[i], hy[i], din, dout, dir=-1)
+            plan.exec_host(hy[i], hz[i], din, dout, dir=+1, normalize=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e_steps = max(1, min(args.steps, 5))
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = world * e_steps * bytes_per_step / (e_ms * 1e-3) / 1e9
+    e2e_err = float((torch.linalg.vector_norm(hz[0] - hx[0]) / torch.linalg.vector_norm(hx[0])).item())
+
+    extra = None
+    if not args.no_extra:
+        extra = extra_table(dev, xs[0], P)
+
+    if rank != 0:
+        barrier(world)
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(shape, elem)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "pct_hbm_peak": round(100.0 * value / world / peak, 1),
+        "config": {"workload": "3-D complex64 FFT 256x256x256, forward + normalised inverse, batch of "
+                               f"{B} distinct volumes per step",
+                   "P": P, "order": format_order(order, 3), "regimes": comm["regime"],
+                   "comm_points_total": comm["total"], "l2": "inputs larger than L2 (8 x 128 MiB per step)",
+                   "parallelism": f"replicas x{world}", "input": "U[-1,1) re/im, seeds 1303..1310",
+                   "roundtrip_rel_l2": err},
+        "roofline": {"kernel": "fft_pass_kernel<float,256>", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
+                     "avg_launch_ms": round(avg_launch_ms, 5), "launches_timed": n_timed * 3,
+                     "pass_ms": [round(v, 5) for v in pass_ms]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * B * T * elem,
+                "d2h_bytes_per_step": 2 * B * T * elem, "steps": e_steps, "roundtrip_rel_l2": e2e_err,
+                "api": "mdfft_exec_host"},
+        "clocks": clk,
+        "gpu_launches": args.steps * B * 2 * plan.launches(),
+        "kernel_source_sha256": kernel_hash(),
+    }
+    if extra is not None:
+        line["extra"] = extra
+    print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+def _orders3():
+    out = []
+    import itertools
+    for p2 in itertools.permutations(range(3)):
+        for p3 in itertools.permutations(range(3)):
+            if len({2, p2[2], p3[2]}) == 3:
+                out.append([[0, 1, 2], list(p2), list(p3)])
+    return out
+
+
+def extra_table(dev, x, P):
+    """GB/s of every 3-D transpose order (complex64) and of the best order in
+    complex128, 256^3, forward transforms, 10 timed reps each."""
+    import torch
+
+    from paper_1302_6189_gb300 import Plan, format_order, mdfft_order_search
+
+    per_transform, T = algorithmic_bytes(SHAPE, 8)
+    res = {"orders_c64_gbs": {}, "note": "forward only, 10 reps, same input volume"}
+    y = torch.empty_like(x)
+    for o in _orders3():
+        with Plan(SHAPE, P, o, "c64") as pl:
+            for _ in range(3):
+                pl.exec(x, y)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(10):
+                pl.exec(x, y)
+            b.record()
+            torch.cuda.synchronize(dev)
+            res["orders_c64_gbs"][format_order(o, 3)] = round(10 * per_transform / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
+    x128 = x.to(torch.complex128)
+    y128 = torch.empty_like(x128)
+    best, _ = mdfft_order_search(SHAPE, P, 0)
+    with Plan(SHAPE, P, best, "c128") as pl:
+        for _ in range(2):
+            pl.exec(x128, y128)
+        pl.set_timing(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            pl.exec(x128, y128)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / 5
+        pass_ms, _ = pl.pass_times()
+    flops = 5.0 * T * 24  # nominal 5 T log2 T
+    res["c128"] = {"gbs": round(2 * per_transform / (ms * 1e-3) / 1e9, 1), "ms_per_transform": round(ms, 4),
+                   "nominal_tflops_fp64": round(flops / (ms * 1e-3) / 1e12, 3),
+                   "pass_ms": [round(v, 4) for v in pass_ms]}
+    return res
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

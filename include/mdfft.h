@@ -1,0 +1,218 @@
+/*
+ * mdfft.h -- C ABI of libmdfft: multi-dimensional complex FFTs on one GPU
+ * (sm_103a), computed the way of Duy and Ozaki's row-wise adaptive
+ * decomposition with transpose-order awareness (arXiv:1302.6189).
+ *
+ * The problem statement follows Fig. 4 of the paper: input X(N_1..N_M), a
+ * number of processes Np and a transpose order; output Xbar(N_1..N_M), the
+ * unnormalised M-D DFT of Sec. 2 (forward sign exp(-2 pi i / N)).  On one
+ * GPU the Np "processes" are virtual partitions of the row-wise flattened
+ * array: they decide the communication amounts reported by
+ * mdfft_comm_volume() and counted on the device by mdfft_exec_counted(),
+ * not the result, which is the same for every Np and every order.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are dense row-major complex arrays in device memory; complex64 is
+ *    (float re, float im), complex128 is (double re, double im).  The natural
+ *    layout has axis a slowest and the last axis fastest.
+ *  - An order is M layouts x M axis ids (0 = a, 1 = b, ...), each layout
+ *    listed from the slowest to the fastest axis.  Layout 0 must be the
+ *    natural 0, 1, ..., M-1, and the last entries of the M layouts must be a
+ *    permutation of 0..M-1 (each step transforms a new axis; Sec. 3.2, the
+ *    C_MD count).  Step s transforms the last axis of layout s and writes the
+ *    result in layout s+1 (the "transpose" of Fig. 4); the last step writes
+ *    the natural layout.
+ *  - Every call returns an mdfft_status; nothing throws across the ABI.  On
+ *    failure mdfft_last_error() returns a message for the calling thread.
+ *  - Execution is asynchronous on the caller's CUDA stream.  Device memory
+ *    passed in stays owned by the caller; the plan owns its own device
+ *    memory (twiddles, workspace) and frees it in mdfft_destroy().
+ *  - A plan may be used from one host thread at a time.
+ */
+#ifndef MDFFT_H
+#define MDFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDFFT_MAX_DIMS 8
+
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st *mdfft_stream_t;
+
+typedef struct mdfft_plan_s *mdfft_plan_t;
+
+typedef enum {
+    MDFFT_OK = 0,
+    MDFFT_E_ARG = -1,         /* bad pointer, size or flag */
+    MDFFT_E_ORDER = -2,       /* order violates the layout rules above */
+    MDFFT_E_RANGE = -3,       /* Np < 1 or Np > N_1 ... N_M (f_MD undefined) */
+    MDFFT_E_NOMEM = -4,       /* host or device allocation failed */
+    MDFFT_E_CUDA = -5,        /* a CUDA runtime call failed */
+    MDFFT_E_TIMEOUT = -6,     /* a bounded device wait gave up */
+    MDFFT_E_UNSUPPORTED = -7  /* size, dtype or M not built into this library */
+} mdfft_status;
+
+typedef enum {
+    MDFFT_C64 = 0,         /* complex64, FP32 arithmetic */
+    MDFFT_C128 = 1,        /* complex128, FP64 arithmetic */
+    MDFFT_C64_TC_FP16 = 2, /* complex64 in/out; radix-16 stages on tensor cores, split hi/lo FP16, FP32 accumulate */
+    MDFFT_C64_TC_BF16 = 3  /* as above with BF16 hi/lo operands */
+} mdfft_dtype;
+
+/* mdfft_plan flags */
+#define MDFFT_PLAN_HOST_ONLY 0x1u /* planner only: no device memory; exec refused */
+#define MDFFT_PLAN_INPLACE 0x2u   /* allow in_dev == out_dev (one more workspace) */
+
+/*
+ * mdfft_plan -- build a plan for the M-D FFT of dims N[0..M) with Np = P
+ * virtual processes and a transpose order.
+ *   out    receives the plan (owned by the caller, free with mdfft_destroy).
+ *   M      number of dimensions, 2..MDFFT_MAX_DIMS.
+ *   N      the M dims, natural order; each dim must be a supported line
+ *          length (products of 2, 3, 5 up to 1024 that the library was built
+ *          for) unless MDFFT_PLAN_HOST_ONLY is set (then any dim >= 1).
+ *   P      number of virtual processes, 1 <= P <= N_1 ... N_M (f_MD, Sec. 3.2).
+ *   order  M*M axis ids as described above, or NULL for the order with the
+ *          smallest total communication amount (mdfft_order_search).
+ *   dt     an mdfft_dtype.
+ *   flags  MDFFT_PLAN_* bits.
+ * Twiddles are made on the device in FP64 (sincospi) and rounded to the
+ * pass precision.  Errors: E_ARG, E_ORDER, E_RANGE, E_UNSUPPORTED, E_NOMEM,
+ * E_CUDA.
+ */
+mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order,
+                        mdfft_dtype dt, unsigned flags);
+
+/*
+ * mdfft_exec -- run the plan: M fused passes, pass s doing the 1-D FFTs along
+ * the last axis of layout s (Fig. 4, steps 1..M) and storing straight into
+ * layout s+1 (the transposes of Fig. 4; the last one gives natural order).
+ *   in_dev, out_dev  device arrays of N_1 ... N_M elements of the plan's
+ *                    complex type, 16-byte aligned; in_dev is not modified
+ *                    unless in_dev == out_dev (needs MDFFT_PLAN_INPLACE);
+ *                    partial overlap is E_ARG.
+ *   dir        -1 forward (exp(-2 pi i jk/N), as the paper), +1 inverse
+ *              (exp(+2 pi i jk/N)).
+ *   normalize  0: no scaling (the paper drops the factor); 1: scale by 1/T
+ *              (only allowed with dir = +1, giving the exact inverse).
+ *   stream     CUDA stream to launch on.
+ */
+mdfft_status mdfft_exec(mdfft_plan_t plan, const void *in_dev, void *out_dev, int dir, int normalize,
+                        mdfft_stream_t stream);
+
+/*
+ * mdfft_exec_counted -- as mdfft_exec, and every pass also counts on the
+ * device the points its store moves to another virtual process, and the
+ * points exchanged for lines cut between processes.
+ *   counts_dev  device array of 2*M int64 entries, zeroed by this call:
+ *               [s], s < M-1: points whose owner changes from layout s to
+ *               s+1; [M-1]: last layout to natural order; [M+s]: split-line
+ *               amount of step s.  Equal to mdfft_comm_volume's numbers.
+ */
+mdfft_status mdfft_exec_counted(mdfft_plan_t plan, const void *in_dev, void *out_dev, int dir,
+                                int normalize, mdfft_stream_t stream, int64_t *counts_dev);
+
+/* Communication amounts of a plan's order, in data points (Sec. 3, Sec. 4). */
+typedef struct {
+    int64_t per_transition[MDFFT_MAX_DIMS]; /* [s], s < M-1: points whose owner changes from layout s to s+1 */
+    int64_t total;                          /* sum of per_transition: what the order search minimises */
+    int64_t final_to_natural;               /* last layout back to natural order (done, not counted) */
+    int64_t split_line[MDFFT_MAX_DIMS];     /* [s]: sum over lines of layout s cut between k owners of N_axis (k-1) */
+    int64_t paper_total;                    /* total + sum(split_line): comparable with the Sec. 4 closed forms */
+    int regime[MDFFT_MAX_DIMS];             /* [s]: leading dims of layout s that chunks are cut on (f_MD case) */
+    double amount_slab;                     /* Sec. 4 closed forms for the same T and Np: T - T/Np */
+    double amount_pencil;                   /* 2N^3 - 2Np (N^2/Np)^(3/2); NaN unless M = 3 and N_1 = N_2 = N_3 */
+    double amount_volumetric;               /* M N^M (N / (N^M/Np)^(1/M) - 1); NaN unless all dims equal */
+} mdfft_comm;
+
+/*
+ * mdfft_comm_volume -- the plan's amounts, computed on the host by
+ * intersecting chunk boxes (every chunk of a row-major range is a union of
+ * at most 2M-1 axis-aligned boxes).  Works on MDFFT_PLAN_HOST_ONLY plans.
+ */
+mdfft_status mdfft_comm_volume(mdfft_plan_t plan, mdfft_comm *out);
+
+/*
+ * mdfft_chunk -- the index map of Sec. 3.2 for process pid in layout `step`
+ * (0..M-1; M means the natural output layout): x^s = f_MD(pid),
+ * x^e = f_MD(pid+1) - 1 over the dims permuted into that layout, and their
+ * coordinates in the layout's axis order (start_coord/end_coord: M entries
+ * each, may be NULL).  E_ARG if step or pid is out of range.
+ */
+mdfft_status mdfft_chunk(mdfft_plan_t plan, int step, int64_t pid, int64_t *xs, int64_t *xe,
+                         int64_t start_coord[], int64_t end_coord[]);
+
+/* The plan's order (M*M ints), e.g. the one the planner picked for order = NULL. */
+mdfft_status mdfft_plan_order(mdfft_plan_t plan, int *order_out);
+
+/*
+ * mdfft_order_search -- the order with the smallest (want_worst = 0) or
+ * largest (want_worst = 1) total amount over all (M-1)!^M orders (Sec. 3.2,
+ * Table 1), by dynamic programming over (step, layout, transformed axes)
+ * with the pairwise amounts from box intersection.  Ties go to the
+ * lexicographically smallest sequence of layouts.  order_out: M*M ints;
+ * total: the amount.  M <= 6 (E_UNSUPPORTED above).
+ */
+mdfft_status mdfft_order_search(int M, const int64_t N[], int64_t P, int want_worst, int *order_out,
+                                int64_t *total);
+
+/*
+ * Per-pass device timing.  mdfft_pass_timing(plan, 1) clears the record and
+ * makes later executions record a CUDA event on their stream before each
+ * pass and after the last one (events only: no host synchronisation), for up
+ * to MDFFT_TIMING_SLOTS executions (older ones are overwritten); 0 stops.
+ * mdfft_pass_times waits for the recorded executions and writes, for each of
+ * the M passes (cap entries at most), the mean duration in milliseconds over
+ * them; *n_execs (may be NULL) receives how many executions were averaged.
+ */
+#define MDFFT_TIMING_SLOTS 512
+mdfft_status mdfft_pass_timing(mdfft_plan_t plan, int enable);
+mdfft_status mdfft_pass_times(mdfft_plan_t plan, float *ms_out, int cap, int *n_execs);
+
+/*
+ * mdfft_exec_host -- end-to-end call on host memory: copies in_host (T
+ * elements) into dev_in, runs mdfft_exec(dev_in -> dev_out) and copies dev_out
+ * back into out_host, all asynchronously on `stream` (use pinned host memory
+ * for overlap; pageable memory works but the copies then block the host).
+ * dev_in and dev_out are caller-owned device arrays of T elements (they may
+ * be the same array only for MDFFT_PLAN_INPLACE plans).  The host buffers
+ * must stay valid until the stream reaches the end of the call.
+ */
+mdfft_status mdfft_exec_host(mdfft_plan_t plan, const void *in_host, void *out_host, void *dev_in, void *dev_out,
+                             int dir, int normalize, mdfft_stream_t stream);
+
+/* Launch shape of pass s: line length, tile (lines along the output's
+ * fastest axis x lines along the next axis), threads per CTA, CTAs, bytes of
+ * shared memory.  Host information only. */
+typedef struct {
+    int64_t line_length;
+    int tile_g, tile_h, threads, smem_bytes;
+    int64_t ctas;
+    int fft_axis, store_axis;
+} mdfft_pass_info;
+mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out);
+
+/* Device workspace the plan owns, in bytes (0 for host-only plans). */
+mdfft_status mdfft_workspace_size(mdfft_plan_t plan, size_t *bytes);
+
+/* Number of kernel launches one mdfft_exec makes (M). */
+mdfft_status mdfft_launches_per_exec(mdfft_plan_t plan, int *launches);
+
+/* Is line length n built into this library for dtype dt?  1 yes, 0 no. */
+int mdfft_supported_length(int64_t n, mdfft_dtype dt);
+
+mdfft_status mdfft_destroy(mdfft_plan_t plan);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *mdfft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDFFT_H */

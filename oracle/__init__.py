@@ -11,7 +11,8 @@ the paper (Duy and Ozaki, arXiv:1302.6189) it follows, is stated in
 
 * ``fftn`` / ``fft_axis`` / ``fft1d`` -- Sec. 2, the M-D DFT as M single-axis
   steps of the unnormalised 1-D DFT (forward sign -1).
-* ``dft_naive`` -- Sec. 2, the nested M-D sum evaluated point by point.
+* ``dft_naive`` / ``dft_point`` -- Sec. 2, the nested M-D sum evaluated point
+  by point (all points / one point).
 * ``regime`` / ``fmd`` / ``coords`` / ``linear`` / ``chunk`` -- Sec. 3.1-3.2,
   the row-wise map, f_MD and the start/end coordinates.
 * ``owner_array`` / ``comm_volume`` / ``split_line`` -- Sec. 3.1 and 3.3, the
@@ -71,6 +72,7 @@ def _load():
             "orc_fft_axis": (c_int, [P(dbl), c_int, P(i64), c_int, c_int, c_int]),
             "orc_fftnd": (c_int, [P(dbl), c_int, P(i64), c_int, c_int]),
             "orc_dft_naive": (c_int, [P(dbl), P(dbl), c_int, P(i64), c_int]),
+            "orc_dft_point": (c_int, [P(dbl), c_int, P(i64), P(i64), c_int, P(dbl)]),
             "orc_regime": (c_int, [c_int, P(i64), i64]),
             "orc_fmd": (i64, [c_int, P(i64), i64, i64]),
             "orc_coords": (None, [c_int, P(i64), i64, P(i64)]),
@@ -183,6 +185,17 @@ def dft_naive(x, sign=-1):
                                _ptr(y.view(np.float64), ctypes.c_double), M, dims, sign)
     _check(rc, "dft_naive")
     return y
+
+
+def dft_point(x, k, sign=-1):
+    """One output value Xbar(k) of the M-D DFT of the natural-order array x."""
+    x = _as_c128(x)
+    dims, M = _dims(x.shape)
+    kk = (ctypes.c_int64 * M)(*[int(v) for v in k])
+    out = (ctypes.c_double * 2)()
+    rc = _load().orc_dft_point(_ptr(x.view(np.float64), ctypes.c_double), M, dims, kk, sign, out)
+    _check(rc, "dft_point")
+    return complex(out[0], out[1])
 
 
 def fft_fig4(x, P, order, sign=-1):

@@ -234,6 +234,49 @@ int orc_dft_naive(const double *in, double *out, int M, const int64_t *N, int si
     return 0;
 }
 
+/* One output point of the M-D DFT, Xbar(k) = sum_j prod_r w_{N_r}^{j_r k_r} X(j),
+ * with the phase of axis r read from a vector of N_r values exp(sign 2 pi i
+ * (j k_r mod N_r) / N_r).  Used for sampled checks of grids too large for a
+ * full reference transform. */
+int orc_dft_point(const double *in, int M, const int64_t *N, const int64_t *k, int sign, double *out) {
+    if (M < 1 || M > ORC_MAXDIM || (sign != -1 && sign != 1)) return -1;
+    cx *ph[ORC_MAXDIM] = {0};
+    int64_t T = 1;
+    int rc = 0;
+    for (int r = 0; r < M; ++r) {
+        T *= N[r];
+        ph[r] = (cx *)malloc((size_t)N[r] * sizeof(cx));
+        if (!ph[r]) {
+            rc = -4;
+            goto done;
+        }
+        for (int64_t j = 0; j < N[r]; ++j) {
+            double a = ORC_TWO_PI * (double)((j * k[r]) % N[r]) / (double)N[r];
+            ph[r][j].re = cos(a);
+            ph[r][j].im = (double)sign * sin(a);
+        }
+    }
+    {
+        const cx *X = (const cx *)in;
+        int64_t jc[ORC_MAXDIM] = {0};
+        cx acc = {0.0, 0.0};
+        for (int64_t jj = 0; jj < T; ++jj) {
+            cx w = ph[0][jc[0]];
+            for (int r = 1; r < M; ++r) w = cx_mul(w, ph[r][jc[r]]);
+            acc = cx_add(acc, cx_mul(w, X[jj]));
+            for (int r = M - 1; r >= 0; --r) { /* next j in row-major order */
+                if (++jc[r] < N[r]) break;
+                jc[r] = 0;
+            }
+        }
+        out[0] = acc.re;
+        out[1] = acc.im;
+    }
+done:
+    for (int r = 0; r < M; ++r) free(ph[r]);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 4. Row-wise decomposition (Sec. 3.1, Sec. 3.2).                            */
 /* ------------------------------------------------------------------------ */

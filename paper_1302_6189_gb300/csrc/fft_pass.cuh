@@ -1,0 +1,388 @@
+// fft_pass.cuh -- one fused pass of the M-D FFT for sm_103a.
+//
+// A pass is one step of the parallel algorithm of Fig. 4 (Duy and Ozaki,
+// arXiv:1302.6189) together with the transpose that follows it: the 1-D
+// DFTs (Sec. 2) along f, the fastest axis of the input layout, and the
+// redistribution of the result into the output layout, whose fastest axis g
+// is a different axis.  On one GPU the transpose is the store itself.
+//
+// Tiling.  A CTA owns a tile of lines: Bg lines that are consecutive along g
+// times Bh lines consecutive along h (the next axis of the output layout).
+//  1. load   each line is contiguous in the input (stride 1 along f), so the
+//            first radix stage reads straight from HBM into registers with
+//            warp-contiguous accesses (or, for very short lines, the tile is
+//            first copied into shared memory);
+//  2. FFT    Stockham autosort stages, radices 16/8/4/2/5/3, one butterfly
+//            per thread per stage in registers, padded shared memory between
+//            stages; twiddles w_N^q come from a table made in FP64;
+//  3. store  the last stage writes the tile transposed ([k][line]) into
+//            shared memory; every thread then owns one line and writes its
+//            k values, so a warp writes runs of Bg consecutive elements of
+//            the output layout's fastest axis.
+// Inverse transforms conjugate on load and on store (conj(DFT(conj x)) is
+// the exp(+2 pi i/N) sum); `scale` multiplies the stored values.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdfft {
+
+constexpr int kMaxTileDims = 8;
+
+// Owner of a row-major index x of a layout under f_MD chunks (Sec. 3.2):
+// with q = x / tail (the index over the `lead` product of the leading dims
+// the chunks are cut on), owner = floor(((q + 1) P - 1) / lead).
+struct OwnerMap {
+    int64_t tail, lead, P;
+};
+
+struct PassArgs {
+    const void *in;
+    void *out;
+    const void *tw;                 // N twiddles w_N^q, q < N, forward sign, pass precision
+    int64_t gblocks, hblocks;       // tiles along g and along h
+    int nrest;                      // remaining axes (not f, g, h), one tile unit each
+    int64_t rest_count[kMaxTileDims];
+    int64_t rest_in[kMaxTileDims];  // input stride of that axis (elements)
+    int64_t rest_out[kMaxTileDims]; // output stride
+    int Bg, Bh;                     // lines per tile along g and h
+    int64_t Ng, Nh;                 // extents of g and h (ragged last tiles are masked)
+    int64_t in_sg, in_sh;           // input strides of g and h
+    int64_t out_sh, out_sf;         // output strides of h and f (g has output stride 1)
+    int conj;                       // 1: inverse
+    double scale;                   // multiplies every stored value
+    unsigned long long *moved;      // count mode: points whose owner changes (null: off)
+    unsigned long long *split;      // count mode: split-line amount of the input layout
+    OwnerMap own_in, own_out;
+};
+
+// ------------------------------------------------------------------ radix plans
+
+struct RadixPlan {
+    int S;       // stages
+    int R[12];   // radix of each stage
+    int maxR;
+};
+
+__host__ __device__ constexpr RadixPlan radix_plan(int n) {
+    RadixPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, 1};
+    int e = 0;
+    while (n % 2 == 0) n /= 2, ++e;
+    // powers of two: as few stages as radix 16 allows, balanced
+    const int pw[11][3] = {{0, 0, 0},  {2, 0, 0},  {4, 0, 0},  {8, 0, 0},  {16, 0, 0}, {8, 4, 0},
+                           {8, 8, 0},  {16, 8, 0}, {16, 16, 0}, {8, 8, 8}, {16, 8, 8}};
+    if (e <= 10)
+        for (int i = 0; i < 3; ++i)
+            if (pw[e][i]) p.R[p.S++] = pw[e][i];
+    while (n % 5 == 0) p.R[p.S++] = 5, n /= 5;
+    while (n % 3 == 0) p.R[p.S++] = 3, n /= 3;
+    for (int i = 0; i < p.S; ++i) p.maxR = p.R[i] > p.maxR ? p.R[i] : p.maxR;
+    if (n != 1 || e > 10) p.S = -1;  // unsupported length
+    return p;
+}
+
+template <typename Real> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+// Launch configuration of the pass kernel for line length N.
+template <typename Real, int N> struct PassCfg {
+    using C = typename Cx<Real>::T;
+    static constexpr RadixPlan plan = radix_plan(N);
+    static_assert(plan.S >= 0, "unsupported line length");  // S = 0: N = 1, a pure redistribution
+    static constexpr int TL = N / plan.maxR;  // threads per line
+    static constexpr int kTileElems = sizeof(Real) == 4 ? 4096 : 2048;
+    // lines per tile: a power of two near kTileElems / N, at least 8, and a
+    // whole number of warps per CTA
+    static constexpr int lines_for() {
+        int l = 8;
+        while (l < 256 && 2 * l * N <= kTileElems) l *= 2;
+        while ((TL * l) % 32 != 0) l *= 2;
+        return l;
+    }
+    static constexpr int LINES = lines_for();
+    static_assert(TL * LINES <= 1024, "CTA too large");
+    static constexpr int THREADS = TL * LINES;
+    static constexpr int PADN = N + N / 16 + 1;  // padded line stride in the stage buffer
+    static constexpr int TROW = LINES + 1;       // padded row of the transposed tile
+    static constexpr int DATA = LINES * PADN > N * TROW ? LINES * PADN : N * TROW;
+    static constexpr size_t SMEM = (size_t)(DATA + N) * sizeof(C) + (size_t)LINES * sizeof(int64_t);
+    static constexpr bool DIRECT = TL * (int)sizeof(C) >= 32;  // first stage loads from HBM directly
+};
+
+// ------------------------------------------------------------------ complex helpers
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// w_16^k = cos(2 pi k/16) - i sin(2 pi k/16), k < 8: cosines and sines of
+// multiples of pi/8
+__host__ __device__ constexpr double cos16(int k) {
+    return k == 0 ? 1.0
+         : k == 1 ? 0.92387953251128675613
+         : k == 2 ? 0.70710678118654752440
+         : k == 3 ? 0.38268343236508977173
+         : k == 4 ? 0.0
+         : k == 5 ? -0.38268343236508977173
+         : k == 6 ? -0.70710678118654752440
+                  : -0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin16(int k) { return cos16(k <= 4 ? 4 - k : k - 4); }  // sin(k pi/8) = cos((4-k) pi/8)
+
+// x * w_16^K for a compile-time K in [0, 8)
+template <int K, typename C> __device__ __forceinline__ C rot16(C x) {
+    using R = decltype(x.x);
+    if constexpr (K == 0) {
+        return x;
+    } else if constexpr (K == 4) {  // -i
+        return {x.y, -x.x};
+    } else if constexpr (K == 2) {  // (1 - i)/sqrt(2)
+        const R h = (R)0.70710678118654752440;
+        return {(x.x + x.y) * h, (x.y - x.x) * h};
+    } else if constexpr (K == 6) {  // (-1 - i)/sqrt(2)
+        const R h = (R)0.70710678118654752440;
+        return {(x.y - x.x) * h, -(x.x + x.y) * h};
+    } else {
+        const R c = (R)cos16(K), s = (R)sin16(K);
+        return {x.x * c + x.y * s, x.y * c - x.x * s};
+    }
+}
+
+// radix-2 decimation in time: v = DFT_R(v), R a power of two <= 16
+template <int R, typename C> struct DftPow2 {
+    template <int K> __device__ __forceinline__ static void combine(C (&v)[R], const C (&e)[R / 2],
+                                                                    const C (&o)[R / 2]) {
+        if constexpr (K < R / 2) {
+            C t = rot16<K * (16 / R)>(o[K]);
+            v[K] = cadd(e[K], t);
+            v[K + R / 2] = csub(e[K], t);
+            combine<K + 1>(v, e, o);
+        }
+    }
+    __device__ __forceinline__ static void run(C (&v)[R]) {
+        if constexpr (R == 2) {
+            C a = v[0], b = v[1];
+            v[0] = cadd(a, b);
+            v[1] = csub(a, b);
+        } else {
+            C e[R / 2], o[R / 2];
+#pragma unroll
+            for (int i = 0; i < R / 2; ++i) e[i] = v[2 * i], o[i] = v[2 * i + 1];
+            DftPow2<R / 2, C>::run(e);
+            DftPow2<R / 2, C>::run(o);
+            combine<0>(v, e, o);
+        }
+    }
+};
+
+template <typename C> __device__ __forceinline__ void dft3(C (&v)[3]) {
+    using R = decltype(v[0].x);
+    const R s = (R)0.86602540378443864676;  // sin(2 pi / 3)
+    C t1 = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    C m = {v[0].x - (R)0.5 * t1.x, v[0].y - (R)0.5 * t1.y};
+    v[0] = cadd(v[0], t1);
+    // -i s d and +i s d
+    v[1] = {m.x + s * d.y, m.y - s * d.x};
+    v[2] = {m.x - s * d.y, m.y + s * d.x};
+}
+
+template <typename C> __device__ __forceinline__ void dft5(C (&v)[5]) {
+    using R = decltype(v[0].x);
+    const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
+    const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
+    C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    C x0 = v[0];
+    C p1 = {x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y};
+    C p2 = {x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y};
+    C q1 = {s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y};  // X1 = p1 - i q1, X4 = p1 + i q1
+    C q2 = {s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y};  // X2 = p2 - i q2, X3 = p2 + i q2
+    v[0] = {x0.x + a1.x + a2.x, x0.y + a1.y + a2.y};
+    v[1] = {p1.x + q1.y, p1.y - q1.x};
+    v[4] = {p1.x - q1.y, p1.y + q1.x};
+    v[2] = {p2.x + q2.y, p2.y - q2.x};
+    v[3] = {p2.x - q2.y, p2.y + q2.x};
+}
+
+template <int R, typename C> __device__ __forceinline__ void dft(C (&v)[R]) {
+    if constexpr (R == 3) dft3(v);
+    else if constexpr (R == 5) dft5(v);
+    else DftPow2<R, C>::run(v);
+}
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
+    unsigned __int128 q = (unsigned __int128)(x / m.tail);
+    return (int64_t)(((q + 1) * (unsigned __int128)m.P - 1) / (unsigned __int128)m.lead);
+}
+
+// ------------------------------------------------------------------ stages
+
+// One Stockham stage with radix R after NS points already combined.
+// Butterfly j (< N/R) reads x[j + r N/R], applies w_{NS R}^{(j mod NS) r},
+// does DFT_R and writes y[(j / NS) NS R + j mod NS + r NS].
+template <typename Real, int N, int SI, int NS> struct Stages {
+    using Cfg = PassCfg<Real, N>;
+    using C = typename Cfg::C;
+    static constexpr int R = Cfg::plan.R[SI];
+    static constexpr int NB = N / R;
+    static constexpr int PER = (NB + Cfg::TL - 1) / Cfg::TL;
+    static constexpr bool FIRST = SI == 0;
+    static constexpr bool LAST = SI == Cfg::plan.S - 1;
+
+    // gsrc: this thread's line in HBM (first stage, direct loads) or null
+    __device__ __forceinline__ static void run(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
+                                               bool ok, bool conj) {
+        C v[PER][R];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int j = t + i * Cfg::TL;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if ((NB % Cfg::TL == 0 || j < NB) && ok) {
+                    if constexpr (FIRST && Cfg::DIRECT) {
+                        C x = __ldg(gsrc + j + r * NB);
+                        if (conj) x.y = -x.y;
+                        v[i][r] = x;
+                    } else {
+                        v[i][r] = buf[line * Cfg::PADN + pad16(j + r * NB)];
+                    }
+                } else {
+                    v[i][r] = C{0, 0};
+                }
+            }
+        }
+        if constexpr (!(FIRST && Cfg::DIRECT)) __syncthreads();  // all reads of buf before any write
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int j = t + i * Cfg::TL;
+            if ((NB % Cfg::TL == 0 || j < NB) && ok) {
+                const int k = j % NS;
+                if constexpr (NS > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], tw[k * r * (N / (NS * R))]);
+                }
+                dft<R>(v[i]);
+                const int base = (j / NS) * NS * R + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if constexpr (LAST) {
+                        tile[(base + r * NS) * Cfg::TROW + line] = v[i][r];
+                    } else {
+                        buf[line * Cfg::PADN + pad16(base + r * NS)] = v[i][r];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (!LAST) Stages<Real, N, SI + 1, NS * R>::run(buf, tile, tw, gsrc, line, t, ok, conj);
+    }
+};
+
+// ------------------------------------------------------------------ the kernel
+
+template <typename Real, int N>
+__global__ void __launch_bounds__(PassCfg<Real, N>::THREADS) fft_pass_kernel(const PassArgs a) {
+    using Cfg = PassCfg<Real, N>;
+    using C = typename Cfg::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
+    C *tw = buf + Cfg::DATA;
+    int64_t *lbase = reinterpret_cast<int64_t *>(tw + N);  // input offset of each line of the tile
+
+    const int tid = threadIdx.x;
+    const C *in = reinterpret_cast<const C *>(a.in);
+    C *out = reinterpret_cast<C *>(a.out);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+
+    // tile coordinates
+    int64_t t = blockIdx.x;
+    const int64_t gb = t % a.gblocks;
+    t /= a.gblocks;
+    const int64_t hb = t % a.hblocks;
+    t /= a.hblocks;
+    const int64_t g0 = gb * a.Bg, h0 = hb * a.Bh;
+    int64_t in_base = g0 * a.in_sg + h0 * a.in_sh;
+    int64_t out_base = g0 + h0 * a.out_sh;
+    for (int i = 0; i < a.nrest; ++i) {
+        const int64_t c = t % a.rest_count[i];
+        t /= a.rest_count[i];
+        in_base += c * a.rest_in[i];
+        out_base += c * a.rest_out[i];
+    }
+
+    for (int q = tid; q < N; q += Cfg::THREADS) tw[q] = gtw[q];
+    if (tid < Cfg::LINES) {
+        const int bg = tid % a.Bg, bh = tid / a.Bg;
+        lbase[tid] = in_base + bg * a.in_sg + bh * a.in_sh;
+    }
+    __syncthreads();
+
+    // FFT role: thread (line, t) with t fastest
+    const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
+    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    const bool fok = line < a.Bg * a.Bh && g0 + fbg < a.Ng && h0 + fbh < a.Nh;
+
+    if constexpr (!Cfg::DIRECT) {  // stage the whole tile through shared memory
+        for (int e = tid; e < Cfg::LINES * N; e += Cfg::THREADS) {
+            const int l = e / N, i = e % N;
+            const int bg = l % a.Bg, bh = l / a.Bg;
+            if (l < a.Bg * a.Bh && g0 + bg < a.Ng && h0 + bh < a.Nh) {
+                C x = in[lbase[l] + i];
+                if (a.conj) x.y = -x.y;
+                buf[l * Cfg::PADN + pad16(i)] = x;
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (Cfg::plan.S == 0) {  // length-1 lines: the DFT is the identity
+        const C v = buf[line * Cfg::PADN];
+        __syncthreads();
+        buf[line] = v;  // tile[k = 0][line]
+        __syncthreads();
+    } else {
+        const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
+        Stages<Real, N, 0, 1>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0);
+    }
+
+    // store role: thread owns line sl and writes k = k0, k0 + TL, ...
+    const int sl = tid % Cfg::LINES, k0 = tid / Cfg::LINES;
+    const int sbg = sl % a.Bg, sbh = sl / a.Bg;
+    const bool sok = sl < a.Bg * a.Bh && g0 + sbg < a.Ng && h0 + sbh < a.Nh;
+    unsigned long long moved = 0, split = 0;
+    if (sok) {
+        const int64_t obase = out_base + sbh * a.out_sh + sbg;
+        const Real sc = (Real)a.scale;
+#pragma unroll 4
+        for (int k = k0; k < N; k += Cfg::TL) {
+            C v = buf[k * Cfg::TROW + sl];
+            if (a.conj) v.y = -v.y;
+            v.x *= sc, v.y *= sc;
+            out[obase + k * a.out_sf] = v;
+        }
+        if (a.moved) {  // count mode: owner of the point before and after the store
+            const int64_t ib = lbase[sl];
+            for (int k = k0; k < N; k += Cfg::TL)
+                moved += owner_of(a.own_in, ib + k) != owner_of(a.own_out, obase + k * a.out_sf);
+            if (k0 == 0) split = (unsigned long long)N * (owner_of(a.own_in, ib + N - 1) - owner_of(a.own_in, ib));
+        }
+    }
+    if (a.moved) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            moved += __shfl_down_sync(0xffffffffu, moved, o);
+            split += __shfl_down_sync(0xffffffffu, split, o);
+        }
+        if ((tid & 31) == 0) {
+            if (moved) atomicAdd(a.moved, moved);
+            if (split) atomicAdd(a.split, split);
+        }
+    }
+}
+
+}  // namespace mdfft

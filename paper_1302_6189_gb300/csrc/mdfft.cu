@@ -1,0 +1,557 @@
+// mdfft.cu -- C ABI of libmdfft (see include/mdfft.h).
+//
+// A plan holds the transpose order, one fused pass per step of Fig. 4
+// (Duy and Ozaki, arXiv:1302.6189) and the device resources the passes use:
+// twiddle tables made in FP64 on the device and one workspace array.  Pass s
+// reads layout s, transforms its last axis and stores layout s+1 (natural
+// order after the last step).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mdfft.h"
+#include "passes.h"
+#include "planner.h"
+
+using mdfft::PassArgs;
+using mdfft::PassKernel;
+namespace pl = mdfft::planner;
+
+namespace {
+
+thread_local std::string g_err;
+
+mdfft_status fail(mdfft_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+mdfft_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(MDFFT_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct Pass {
+    int f = 0, g = 0, h = -1;  // transformed axis, output's fastest axis, next tile axis
+    int64_t n = 0;             // line length N_f
+    PassKernel k{};
+    PassArgs args{};           // everything but in/out/tw/conj/scale/count pointers
+    int64_t ctas = 0;
+    size_t tw_offset = 0;      // byte offset of this pass's twiddle table
+};
+
+}  // namespace
+
+struct mdfft_plan_s {
+    int M = 0;
+    int64_t N[MDFFT_MAX_DIMS] = {0};
+    int64_t P = 0, T = 0;
+    mdfft_dtype dt = MDFFT_C64;
+    unsigned flags = 0;
+    size_t elem = 8;
+    std::vector<pl::Layout> order;
+    Pass pass[MDFFT_MAX_DIMS];
+    void *tw = nullptr, *ws = nullptr, *ws2 = nullptr;
+    size_t tw_bytes = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // MDFFT_TIMING_SLOTS x (M + 1) events, made on first enable
+    int64_t timed = 0;            // executions recorded since the last enable
+    bool comm_ready = false;
+    mdfft_comm comm{};
+};
+
+namespace {
+
+// strides of every natural axis in layout L
+void layout_strides(const pl::Layout &L, const int64_t *N, int64_t *stride) {
+    int64_t s = 1;
+    for (int i = L.M - 1; i >= 0; --i) {
+        stride[L.axis[i]] = s;
+        s *= N[L.axis[i]];
+    }
+}
+
+mdfft::OwnerMap owner_map(int M, const int64_t *N, int64_t P, const pl::Layout &L) {
+    int64_t d[pl::kMaxDims];
+    pl::layout_dims(L, N, d);
+    int k = pl::regime(M, d, P);
+    mdfft::OwnerMap m{1, 1, P};
+    for (int i = 0; i < M; ++i) (i < k ? m.lead : m.tail) *= d[i];
+    return m;
+}
+
+bool lookup(mdfft_dtype dt, int64_t n, PassKernel *k) {
+    if (dt == MDFFT_C64) return mdfft::find_pass_kernel_c64(n, k);
+    if (dt == MDFFT_C128) return mdfft::find_pass_kernel_c128(n, k);
+    return false;
+}
+
+// Tile shape: Bg lines along g times Bh along h, at most `lines`, scored by
+// the fraction of useful lines and by the length of the contiguous runs the
+// store writes (a run of Bg elements; 128 bytes and more count as full).
+void choose_tile(int lines, int64_t Ng, int64_t Nh, size_t elem, int *Bg, int *Bh) {
+    double best = -1;
+    for (int bg = 1; bg <= lines && bg <= Ng; ++bg) {
+        int bh = (int)std::min<int64_t>(Nh, lines / bg);
+        if (bh < 1) continue;
+        double ug = (double)Ng / (double)(((Ng + bg - 1) / bg) * bg);
+        double uh = (double)Nh / (double)(((Nh + bh - 1) / bh) * bh);
+        double fill = (double)(bg * bh) / (double)lines;
+        double coal = std::min(1.0, (double)bg * (double)elem / 128.0);
+        double score = ug * uh * fill * coal;
+        if (score > best + 1e-12) best = score, *Bg = bg, *Bh = bh;
+    }
+}
+
+mdfft_status build_pass(mdfft_plan_s *p, int s) {
+    const int M = p->M;
+    const pl::Layout &L = p->order[s];
+    pl::Layout nat;
+    nat.M = M;
+    for (int i = 0; i < M; ++i) nat.axis[i] = i;
+    const pl::Layout &Lo = (s + 1 < M) ? p->order[s + 1] : nat;
+    Pass &ps = p->pass[s];
+    ps.f = L.axis[M - 1];
+    ps.g = Lo.axis[M - 1];
+    if (ps.g == ps.f) return fail(MDFFT_E_ORDER, "output layout keeps the transformed axis fastest");
+    ps.h = -1;
+    for (int i = M - 2; i >= 0; --i)
+        if (Lo.axis[i] != ps.f) {
+            ps.h = Lo.axis[i];
+            break;
+        }
+    ps.n = p->N[ps.f];
+    if (!lookup(p->dt, ps.n, &ps.k))
+        return fail(MDFFT_E_UNSUPPORTED, "line length " + std::to_string(ps.n) + " is not built for this dtype");
+
+    int64_t sin_[pl::kMaxDims], sout[pl::kMaxDims];
+    layout_strides(L, p->N, sin_);
+    layout_strides(Lo, p->N, sout);
+    PassArgs &a = ps.args;
+    std::memset(&a, 0, sizeof(a));
+    const int64_t Ng = p->N[ps.g], Nh = ps.h >= 0 ? p->N[ps.h] : 1;
+    int Bg = 1, Bh = 1;
+    choose_tile(ps.k.lines, Ng, Nh, p->elem, &Bg, &Bh);
+    a.Bg = Bg, a.Bh = Bh, a.Ng = Ng, a.Nh = Nh;
+    a.gblocks = (Ng + Bg - 1) / Bg;
+    a.hblocks = (Nh + Bh - 1) / Bh;
+    a.in_sg = sin_[ps.g];
+    a.in_sh = ps.h >= 0 ? sin_[ps.h] : 0;
+    a.out_sh = ps.h >= 0 ? sout[ps.h] : 0;
+    a.out_sf = sout[ps.f];
+    if (sout[ps.g] != 1 || sin_[ps.f] != 1) return fail(MDFFT_E_ORDER, "internal: layout strides");
+    // remaining axes, fastest first in the output layout
+    a.nrest = 0;
+    ps.ctas = a.gblocks * a.hblocks;
+    for (int i = M - 1; i >= 0; --i) {
+        int ax = Lo.axis[i];
+        if (ax == ps.f || ax == ps.g || ax == ps.h) continue;
+        a.rest_count[a.nrest] = p->N[ax];
+        a.rest_in[a.nrest] = sin_[ax];
+        a.rest_out[a.nrest] = sout[ax];
+        a.nrest++;
+        ps.ctas *= p->N[ax];
+    }
+    a.own_in = owner_map(M, p->N, p->P, L);
+    a.own_out = owner_map(M, p->N, p->P, Lo);
+    a.scale = 1.0;
+    return MDFFT_OK;
+}
+
+__global__ void twiddle_kernel(void *dst, int64_t n, int dbl) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)q / (double)n, &s, &c);  // w_n^q = exp(-2 pi i q / n)
+    if (dbl) reinterpret_cast<double2 *>(dst)[q] = make_double2(c, s);
+    else reinterpret_cast<float2 *>(dst)[q] = make_float2((float)c, (float)s);
+}
+
+mdfft_status parse_order(int M, const int *order, std::vector<pl::Layout> &out) {
+    out.clear();
+    for (int s = 0; s < M; ++s) {
+        pl::Layout L;
+        L.M = M;
+        for (int i = 0; i < M; ++i) L.axis[i] = order[s * M + i];
+        out.push_back(L);
+    }
+    std::string msg = pl::check_order(M, out);
+    if (!msg.empty()) return fail(MDFFT_E_ORDER, msg);
+    return MDFFT_OK;
+}
+
+void release(mdfft_plan_s *p) {
+    if (!p) return;
+    if (p->tw) cudaFree(p->tw);
+    if (p->ws) cudaFree(p->ws);
+    if (p->ws2) cudaFree(p->ws2);
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+bool overlaps(const void *a, const void *b, size_t n) {
+    auto x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
+}
+
+mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, mdfft_stream_t stream,
+                       int64_t *counts) {
+    if (!p) return fail(MDFFT_E_ARG, "null plan");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan cannot execute");
+    if (!in || !out) return fail(MDFFT_E_ARG, "null data pointer");
+    if (dir != -1 && dir != 1) return fail(MDFFT_E_ARG, "dir must be -1 (forward) or +1 (inverse)");
+    if (normalize != 0 && !(normalize == 1 && dir == 1))
+        return fail(MDFFT_E_ARG, "normalize = 1 is only defined for the inverse");
+    size_t align = p->dt == MDFFT_C128 ? 16 : 8;
+    if ((uintptr_t)in % align || (uintptr_t)out % align) return fail(MDFFT_E_ARG, "misaligned data pointer");
+    const size_t bytes = (size_t)p->T * p->elem;
+    const bool inplace = in == out;
+    if (inplace && !(p->flags & MDFFT_PLAN_INPLACE))
+        return fail(MDFFT_E_ARG, "in == out needs a plan made with MDFFT_PLAN_INPLACE");
+    if (!inplace && overlaps(in, out, bytes)) return fail(MDFFT_E_ARG, "in and out overlap partially");
+    if (counts && ((uintptr_t)counts % 8)) return fail(MDFFT_E_ARG, "misaligned counts pointer");
+
+    const int M = p->M;
+    // destination of every pass: the last one is `out`; going backwards the
+    // buffers alternate so that no pass reads and writes the same array and
+    // `in` is never written (unless in == out)
+    void *dst[MDFFT_MAX_DIMS];
+    dst[M - 1] = out;
+    for (int s = M - 2; s >= 0; --s) dst[s] = (dst[s + 1] == out) ? p->ws : out;
+    if (dst[0] == in) dst[0] = p->ws2;  // in-place with an odd number of passes
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (counts) {
+        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * M, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    const void *src = in;
+    const int64_t slot = p->timed % MDFFT_TIMING_SLOTS;
+    for (int s = 0; s < M; ++s) {
+        Pass &ps = p->pass[s];
+        PassArgs a = ps.args;
+        a.in = src;
+        a.out = dst[s];
+        a.tw = (const char *)p->tw + ps.tw_offset;
+        a.conj = dir == 1;
+        a.scale = (s == M - 1 && normalize) ? 1.0 / (double)p->T : 1.0;
+        if (counts) {
+            a.moved = reinterpret_cast<unsigned long long *>(counts + s);
+            a.split = reinterpret_cast<unsigned long long *>(counts + M + s);
+        }
+        if (p->timing) cudaEventRecord(p->ev[slot * (M + 1) + s], st);
+        void *args[] = {&a};
+        cudaError_t e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)ps.ctas), dim3(ps.k.threads), args, ps.k.smem, st);
+        if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+        src = dst[s];
+    }
+    if (p->timing) {
+        cudaEventRecord(p->ev[slot * (M + 1) + M], st);
+        p->timed++;
+    }
+    return MDFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mdfft_last_error(void) { return g_err.c_str(); }
+
+int mdfft_supported_length(int64_t n, mdfft_dtype dt) {
+    PassKernel k;
+    return lookup(dt, n, &k) ? 1 : 0;
+}
+
+mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order, mdfft_dtype dt,
+                        unsigned flags) {
+    g_err.clear();
+    if (!out || !N) return fail(MDFFT_E_ARG, "null argument");
+    *out = nullptr;
+    if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
+    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE)) return fail(MDFFT_E_ARG, "unknown flag");
+    if (dt != MDFFT_C64 && dt != MDFFT_C128) {
+        if (dt == MDFFT_C64_TC_FP16 || dt == MDFFT_C64_TC_BF16)
+            return fail(MDFFT_E_UNSUPPORTED, "tensor-core dtypes are not built");
+        return fail(MDFFT_E_ARG, "unknown dtype");
+    }
+    mdfft_plan_s *p = new (std::nothrow) mdfft_plan_s;
+    if (!p) return fail(MDFFT_E_NOMEM, "host allocation");
+    p->M = M, p->P = P, p->dt = dt, p->flags = flags;
+    p->elem = dt == MDFFT_C128 ? 16 : 8;
+    unsigned __int128 T = 1;
+    for (int i = 0; i < M; ++i) {
+        if (N[i] < 1) {
+            release(p);
+            return fail(MDFFT_E_ARG, "dims must be >= 1");
+        }
+        p->N[i] = N[i];
+        T *= (unsigned __int128)N[i];
+    }
+    if (T > ((unsigned __int128)1 << 40)) {
+        release(p);
+        return fail(MDFFT_E_ARG, "grid too large");
+    }
+    p->T = (int64_t)T;
+    if (P < 1 || P > p->T) {
+        release(p);
+        return fail(MDFFT_E_RANGE, "P must be in [1, N_1 ... N_M]");
+    }
+    mdfft_status st;
+    if (order) {
+        if ((st = parse_order(M, order, p->order)) != MDFFT_OK) {
+            release(p);
+            return st;
+        }
+    } else {
+        int64_t total;
+        std::string err;
+        if (!pl::search_order(M, p->N, P, false, p->order, total, err)) {
+            release(p);
+            return fail(MDFFT_E_UNSUPPORTED, "order search: " + err);
+        }
+    }
+    const bool host_only = flags & MDFFT_PLAN_HOST_ONLY;
+    if (!host_only) {
+        // every axis is transformed once: its line length must be built
+        for (int i = 0; i < M; ++i) {
+            PassKernel k;
+            if (!lookup(dt, p->N[i], &k)) {
+                release(p);
+                return fail(MDFFT_E_UNSUPPORTED, "line length " + std::to_string(p->N[i]) + " is not built");
+            }
+        }
+        for (int s = 0; s < M; ++s)
+            if ((st = build_pass(p, s)) != MDFFT_OK) {
+                release(p);
+                return st;
+            }
+        // twiddle tables: one per pass, 256-byte aligned inside one allocation
+        size_t off = 0;
+        for (int s = 0; s < M; ++s) {
+            p->pass[s].tw_offset = off;
+            off += ((size_t)p->pass[s].n * p->elem + 255) / 256 * 256;
+        }
+        p->tw_bytes = off;
+        cudaError_t e = cudaMalloc(&p->tw, off);
+        if (e != cudaSuccess) {
+            release(p);
+            return cuda_fail(e, "cudaMalloc twiddles");
+        }
+        for (int s = 0; s < M; ++s) {
+            int64_t n = p->pass[s].n;
+            twiddle_kernel<<<(unsigned)((n + 255) / 256), 256>>>((char *)p->tw + p->pass[s].tw_offset, n,
+                                                                 dt == MDFFT_C128);
+        }
+        const size_t bytes = (size_t)p->T * p->elem;
+        if ((e = cudaMalloc(&p->ws, bytes)) != cudaSuccess) {
+            release(p);
+            return cuda_fail(e, "cudaMalloc workspace");
+        }
+        if ((flags & MDFFT_PLAN_INPLACE) && (M % 2 == 1)) {
+            if ((e = cudaMalloc(&p->ws2, bytes)) != cudaSuccess) {
+                release(p);
+                return cuda_fail(e, "cudaMalloc second workspace");
+            }
+        }
+        for (int s = 0; s < M; ++s) {
+            const PassKernel &k = p->pass[s].k;
+            if (k.smem > 48 * 1024) {
+                e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+                if (e != cudaSuccess) {
+                    release(p);
+                    return cuda_fail(e, "cudaFuncSetAttribute");
+                }
+            }
+        }
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) {  // twiddles ready for any stream
+            release(p);
+            return cuda_fail(e, "twiddle generation");
+        }
+    }
+    *out = p;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_exec(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, mdfft_stream_t stream) {
+    return exec_impl(p, in, out, dir, normalize, stream, nullptr);
+}
+
+mdfft_status mdfft_exec_counted(mdfft_plan_t p, const void *in, void *out, int dir, int normalize,
+                                mdfft_stream_t stream, int64_t *counts_dev) {
+    if (!counts_dev) return fail(MDFFT_E_ARG, "null counts pointer");
+    return exec_impl(p, in, out, dir, normalize, stream, counts_dev);
+}
+
+mdfft_status mdfft_comm_volume(mdfft_plan_t p, mdfft_comm *out) {
+    if (!p || !out) return fail(MDFFT_E_ARG, "null argument");
+    if (!p->comm_ready) {
+        mdfft_comm c;
+        std::memset(&c, 0, sizeof(c));
+        const int M = p->M;
+        pl::Layout nat;
+        nat.M = M;
+        for (int i = 0; i < M; ++i) nat.axis[i] = i;
+        for (int s = 0; s + 1 < M; ++s) {
+            c.per_transition[s] = pl::transition_amount(M, p->N, p->P, p->order[s], p->order[s + 1]);
+            c.total += c.per_transition[s];
+        }
+        c.final_to_natural = pl::transition_amount(M, p->N, p->P, p->order[M - 1], nat);
+        c.paper_total = c.total;
+        for (int s = 0; s < M; ++s) {
+            c.split_line[s] = pl::split_line_amount(M, p->N, p->P, p->order[s]);
+            c.paper_total += c.split_line[s];
+            int64_t d[pl::kMaxDims];
+            pl::layout_dims(p->order[s], p->N, d);
+            c.regime[s] = pl::regime(M, d, p->P);
+        }
+        // Sec. 4 closed forms for the same T and Np
+        const double T = (double)p->T, P = (double)p->P, nan = std::nan("");
+        bool cubic = true;
+        for (int i = 1; i < M; ++i) cubic = cubic && p->N[i] == p->N[0];
+        const double n = (double)p->N[0];
+        c.amount_slab = T - T / P;
+        c.amount_pencil = (cubic && M == 3) ? 2.0 * n * n * n - 2.0 * P * std::pow(n * n / P, 1.5) : nan;
+        c.amount_volumetric = cubic ? (double)M * T * (n / std::pow(T / P, 1.0 / (double)M) - 1.0) : nan;
+        p->comm = c;
+        p->comm_ready = true;
+    }
+    *out = p->comm;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_chunk(mdfft_plan_t p, int step, int64_t pid, int64_t *xs, int64_t *xe, int64_t start_coord[],
+                         int64_t end_coord[]) {
+    if (!p || !xs || !xe) return fail(MDFFT_E_ARG, "null argument");
+    if (step < 0 || step > p->M) return fail(MDFFT_E_ARG, "step out of range");
+    if (pid < 0 || pid >= p->P) return fail(MDFFT_E_ARG, "pid out of range");
+    pl::Layout L;
+    L.M = p->M;
+    for (int i = 0; i < p->M; ++i) L.axis[i] = step < p->M ? p->order[step].axis[i] : i;
+    int64_t d[pl::kMaxDims];
+    pl::layout_dims(L, p->N, d);
+    *xs = pl::fmd(p->M, d, p->P, pid);
+    *xe = pl::fmd(p->M, d, p->P, pid + 1) - 1;
+    if (start_coord) pl::digits(p->M, d, *xs, start_coord);
+    if (end_coord) pl::digits(p->M, d, *xe, end_coord);
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_plan_order(mdfft_plan_t p, int *order_out) {
+    if (!p || !order_out) return fail(MDFFT_E_ARG, "null argument");
+    for (int s = 0; s < p->M; ++s)
+        for (int i = 0; i < p->M; ++i) order_out[s * p->M + i] = p->order[s].axis[i];
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_order_search(int M, const int64_t N[], int64_t P, int want_worst, int *order_out, int64_t *total) {
+    if (!N || !order_out || !total) return fail(MDFFT_E_ARG, "null argument");
+    if (M < 2 || M > 6) return fail(MDFFT_E_UNSUPPORTED, "order search supports 2 <= M <= 6");
+    int64_t T = 1;
+    for (int i = 0; i < M; ++i) {
+        if (N[i] < 1) return fail(MDFFT_E_ARG, "dims must be >= 1");
+        T *= N[i];
+    }
+    if (P < 1 || P > T) return fail(MDFFT_E_RANGE, "P must be in [1, N_1 ... N_M]");
+    std::vector<pl::Layout> order;
+    std::string err;
+    if (!pl::search_order(M, N, P, want_worst != 0, order, *total, err)) return fail(MDFFT_E_ARG, err);
+    for (int s = 0; s < M; ++s)
+        for (int i = 0; i < M; ++i) order_out[s * M + i] = order[s].axis[i];
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_pass_timing(mdfft_plan_t p, int enable) {
+    if (!p) return fail(MDFFT_E_ARG, "null plan");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan");
+    if (enable && p->ev.empty()) {
+        p->ev.assign((size_t)MDFFT_TIMING_SLOTS * (p->M + 1), nullptr);
+        for (cudaEvent_t &e : p->ev) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate");
+        }
+    }
+    p->timing = enable != 0;
+    if (enable) p->timed = 0;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_pass_times(mdfft_plan_t p, float *ms_out, int cap, int *n_execs) {
+    if (!p || !ms_out) return fail(MDFFT_E_ARG, "null argument");
+    if (p->timed == 0) return fail(MDFFT_E_ARG, "no timed execution recorded");
+    const int M = p->M;
+    const int64_t n = std::min<int64_t>(p->timed, MDFFT_TIMING_SLOTS);
+    const int64_t last = (p->timed - 1) % MDFFT_TIMING_SLOTS;
+    cudaError_t e = cudaEventSynchronize(p->ev[last * (M + 1) + M]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    std::vector<double> sum(M, 0.0);
+    for (int64_t slot = 0; slot < n; ++slot)
+        for (int s = 0; s < M; ++s) {
+            float ms = 0;
+            e = cudaEventElapsedTime(&ms, p->ev[slot * (M + 1) + s], p->ev[slot * (M + 1) + s + 1]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+            sum[s] += ms;
+        }
+    for (int s = 0; s < M && s < cap; ++s) ms_out[s] = (float)(sum[s] / (double)n);
+    if (n_execs) *n_execs = (int)n;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_exec_host(mdfft_plan_t p, const void *in_host, void *out_host, void *dev_in, void *dev_out,
+                             int dir, int normalize, mdfft_stream_t stream) {
+    if (!p) return fail(MDFFT_E_ARG, "null plan");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan cannot execute");
+    if (!in_host || !out_host || !dev_in || !dev_out) return fail(MDFFT_E_ARG, "null pointer");
+    const size_t bytes = (size_t)p->T * p->elem;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(dev_in, in_host, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    mdfft_status r = exec_impl(p, dev_in, dev_out, dir, normalize, stream, nullptr);
+    if (r != MDFFT_OK) return r;
+    e = cudaMemcpyAsync(out_host, dev_out, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {
+    if (!p || !out) return fail(MDFFT_E_ARG, "null argument");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan has no passes");
+    if (s < 0 || s >= p->M) return fail(MDFFT_E_ARG, "pass index out of range");
+    const Pass &ps = p->pass[s];
+    out->line_length = ps.n;
+    out->tile_g = ps.args.Bg;
+    out->tile_h = ps.args.Bh;
+    out->threads = ps.k.threads;
+    out->smem_bytes = (int)ps.k.smem;
+    out->ctas = ps.ctas;
+    out->fft_axis = ps.f;
+    out->store_axis = ps.g;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_workspace_size(mdfft_plan_t p, size_t *bytes) {
+    if (!p || !bytes) return fail(MDFFT_E_ARG, "null argument");
+    *bytes = 0;
+    if (p->ws) *bytes += (size_t)p->T * p->elem;
+    if (p->ws2) *bytes += (size_t)p->T * p->elem;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_launches_per_exec(mdfft_plan_t p, int *launches) {
+    if (!p || !launches) return fail(MDFFT_E_ARG, "null argument");
+    *launches = p->M;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_destroy(mdfft_plan_t p) {
+    release(p);
+    return MDFFT_OK;
+}
+
+}  // extern "C"

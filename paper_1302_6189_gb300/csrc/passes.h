@@ -1,0 +1,27 @@
+// passes.h -- registry of the compiled pass kernels (one per line length and precision).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "fft_pass.cuh"
+
+// Line lengths built into the library: 1 and products of 2, 3 and 5 up to
+// 1024 whose radix plan is in fft_pass.cuh.
+#define MDFFT_LENGTHS(X)                                                                                   \
+    X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(15) X(16) X(20) X(24) X(30) X(32) X(40) X(48) X(60) X(64) \
+        X(80) X(96) X(120) X(128) X(160) X(192) X(240) X(256) X(320) X(384) X(480) X(512) X(640) X(768)    \
+            X(960) X(1024)
+
+namespace mdfft {
+
+struct PassKernel {
+    const void *fn;  // __global__ fft_pass_kernel<Real, N>
+    int threads, lines, tl;
+    size_t smem;
+};
+
+bool find_pass_kernel_c64(int64_t n, PassKernel *k);
+bool find_pass_kernel_c128(int64_t n, PassKernel *k);
+
+}  // namespace mdfft

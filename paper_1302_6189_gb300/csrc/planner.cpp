@@ -1,0 +1,260 @@
+// planner.cpp -- row-wise adaptive decomposition planner (host, integers).
+//
+// Follows Sec. 3.1-3.2 of Duy and Ozaki (arXiv:1302.6189): the f_MD chunk
+// function, its start/end coordinates, the communication amount of a
+// transpose (points whose owner changes; the rest are reused, Sec. 1 and the
+// text on Fig. 2) and the order count of the C_MD equation.  Amounts are
+// computed by intersecting the boxes that make up each chunk, and the order
+// search is a dynamic programme over (step, layout, axes already
+// transformed): neither enumerates points or orders.
+#include "planner.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace mdfft {
+namespace planner {
+
+typedef unsigned __int128 u128;
+
+int regime(int M, const int64_t *d, int64_t P) {
+    if (M < 1 || M > kMaxDims || P < 1) return -1;
+    u128 prod = 1;
+    for (int k = 0; k < M; ++k) {
+        if (d[k] < 1) return -1;
+        prod *= (u128)d[k];
+        if ((u128)P <= prod) return k + 1;
+    }
+    return -1;
+}
+
+int64_t fmd(int M, const int64_t *d, int64_t P, int64_t pid) {
+    int k = regime(M, d, P);
+    if (k < 0 || pid < 0 || pid > P) return -1;
+    u128 lead = 1, tail = 1;
+    for (int i = 0; i < M; ++i) (i < k ? lead : tail) *= (u128)d[i];
+    return (int64_t)(((lead * (u128)pid) / (u128)P) * tail);
+}
+
+void digits(int M, const int64_t *d, int64_t x, int64_t *c) {
+    for (int i = M - 1; i >= 0; --i) {
+        c[i] = x % d[i];
+        x /= d[i];
+    }
+}
+
+void layout_dims(const Layout &L, const int64_t *N, int64_t *d) {
+    for (int i = 0; i < L.M; ++i) d[i] = N[L.axis[i]];
+}
+
+int64_t owner_of(int M, const int64_t *N, int64_t P, const Layout &L, int64_t x) {
+    int64_t d[kMaxDims];
+    layout_dims(L, N, d);
+    int k = regime(M, d, P);
+    u128 lead = 1, tail = 1;
+    for (int i = 0; i < M; ++i) (i < k ? lead : tail) *= (u128)d[i];
+    u128 q = (u128)x / tail;  // index over the k leading dims
+    // largest p with floor(lead * p / P) <= q
+    return (int64_t)(((q + 1) * (u128)P - 1) / lead);
+}
+
+// Row-major range [a, b) over dims d (layout order) -> boxes in layout
+// coordinates, recursing from the slowest dim: a partial head slab, a run of
+// whole slabs, a partial tail slab.
+static void boxes_rec(int M, const int64_t *d, int level, int64_t a, int64_t b, int64_t *lo, int64_t *hi,
+                      std::vector<Box> &out, const int *axis) {
+    if (a >= b) return;
+    int64_t stride = 1;
+    for (int i = level + 1; i < M; ++i) stride *= d[i];
+    if (level == M - 1) {
+        lo[level] = a, hi[level] = b;
+        Box bx;
+        for (int i = 0; i < M; ++i) bx.lo[axis[i]] = lo[i], bx.hi[axis[i]] = hi[i];
+        out.push_back(bx);
+        return;
+    }
+    int64_t qa = a / stride, ra = a % stride, qb = b / stride, rb = b % stride;
+    if (qa == qb) {
+        lo[level] = qa, hi[level] = qa + 1;
+        boxes_rec(M, d, level + 1, ra, rb, lo, hi, out, axis);
+        return;
+    }
+    if (ra != 0) {
+        lo[level] = qa, hi[level] = qa + 1;
+        boxes_rec(M, d, level + 1, ra, stride, lo, hi, out, axis);
+        ++qa;
+    }
+    if (qa < qb) {
+        lo[level] = qa, hi[level] = qb;
+        for (int i = level + 1; i < M; ++i) lo[i] = 0, hi[i] = d[i];
+        Box bx;
+        for (int i = 0; i < M; ++i) bx.lo[axis[i]] = lo[i], bx.hi[axis[i]] = hi[i];
+        out.push_back(bx);
+    }
+    if (rb != 0) {
+        lo[level] = qb, hi[level] = qb + 1;
+        boxes_rec(M, d, level + 1, 0, rb, lo, hi, out, axis);
+    }
+}
+
+void range_boxes(const Layout &L, const int64_t *N, int64_t a, int64_t b, std::vector<Box> &out) {
+    int64_t d[kMaxDims], lo[kMaxDims], hi[kMaxDims];
+    layout_dims(L, N, d);
+    boxes_rec(L.M, d, 0, a, b, lo, hi, out, L.axis);
+}
+
+static int64_t overlap(int M, const Box &x, const Box &y) {
+    int64_t v = 1;
+    for (int i = 0; i < M; ++i) {
+        int64_t lo = std::max(x.lo[i], y.lo[i]), hi = std::min(x.hi[i], y.hi[i]);
+        if (hi <= lo) return 0;
+        v *= hi - lo;
+    }
+    return v;
+}
+
+int64_t transition_amount(int M, const int64_t *N, int64_t P, const Layout &A, const Layout &B) {
+    int64_t da[kMaxDims], db[kMaxDims], T = 1;
+    layout_dims(A, N, da);
+    layout_dims(B, N, db);
+    for (int i = 0; i < M; ++i) T *= N[i];
+    int64_t kept = 0;
+    std::vector<Box> ba, bb;
+    for (int64_t p = 0; p < P; ++p) {
+        ba.clear(), bb.clear();
+        range_boxes(A, N, fmd(M, da, P, p), fmd(M, da, P, p + 1), ba);
+        range_boxes(B, N, fmd(M, db, P, p), fmd(M, db, P, p + 1), bb);
+        for (const Box &x : ba)
+            for (const Box &y : bb) kept += overlap(M, x, y);
+    }
+    return T - kept;
+}
+
+int64_t split_line_amount(int M, const int64_t *N, int64_t P, const Layout &L) {
+    // A chunk boundary that is not a multiple of the line length falls
+    // inside a line and gives that line one more owner (chunks are never
+    // empty because P <= T).
+    int64_t d[kMaxDims];
+    layout_dims(L, N, d);
+    int64_t nf = d[M - 1], cuts = 0;
+    for (int64_t p = 1; p < P; ++p) cuts += (fmd(M, d, P, p) % nf) != 0;
+    return nf * cuts;
+}
+
+std::string check_order(int M, const std::vector<Layout> &order) {
+    if ((int)order.size() != M) return "order must have M layouts";
+    bool used_last[kMaxDims] = {false};
+    for (int s = 0; s < M; ++s) {
+        bool seen[kMaxDims] = {false};
+        for (int i = 0; i < M; ++i) {
+            int a = order[s].axis[i];
+            if (a < 0 || a >= M || seen[a]) return "layout " + std::to_string(s) + " is not a permutation";
+            seen[a] = true;
+            if (s == 0 && a != i) return "layout 0 must be the natural order";
+        }
+        int last = order[s].axis[M - 1];
+        if (used_last[last]) return "layout " + std::to_string(s) + " transforms an axis twice";
+        used_last[last] = true;
+    }
+    return "";
+}
+
+// ---------------------------------------------------------------- order search
+
+namespace {
+
+struct SearchCtx {
+    int M;
+    const int64_t *N;
+    int64_t P;
+    bool worst;
+    std::vector<Layout> perms;
+    std::vector<int64_t> pair;     // lazily filled pairwise amounts, -1 = unknown
+    std::vector<int64_t> memo;     // [layer][perm][mask], INT64_MIN = unknown
+    int F, masks;
+
+    int64_t amount(int f, int g) {
+        int64_t &v = pair[(size_t)f * F + g];
+        if (v < 0) v = transition_amount(M, N, P, perms[f], perms[g]);
+        return v;
+    }
+    bool better(int64_t a, int64_t b) const { return worst ? a > b : a < b; }
+
+    int64_t &slot(int layer, int f, unsigned mask) { return memo[((size_t)layer * F + f) * masks + mask]; }
+
+    // optimal sum of transitions from layout f at `layer` to the last layer
+    int64_t solve(int layer, int f, unsigned mask) {
+        if (layer == M - 1) return 0;
+        int64_t &m = slot(layer, f, mask);
+        if (m != INT64_MIN) return m;
+        bool have = false;
+        int64_t best = 0;
+        for (int g = 0; g < F; ++g) {
+            int last = perms[g].axis[M - 1];
+            if (mask & (1u << last)) continue;
+            int64_t v = amount(f, g) + solve(layer + 1, g, mask | (1u << last));
+            if (!have || better(v, best)) best = v, have = true;
+        }
+        m = best;
+        return m;
+    }
+};
+
+}  // namespace
+
+bool search_order(int M, const int64_t *N, int64_t P, bool want_worst, std::vector<Layout> &order,
+                  int64_t &total, std::string &err) {
+    if (M < 2 || M > 6) {
+        err = "order search supports 2 <= M <= 6";
+        return false;
+    }
+    int64_t T = 1;
+    for (int i = 0; i < M; ++i) {
+        if (N[i] < 1) {
+            err = "dims must be >= 1";
+            return false;
+        }
+        T *= N[i];
+    }
+    if (P < 1 || P > T) {
+        err = "P out of range";
+        return false;
+    }
+    SearchCtx c;
+    c.M = M, c.N = N, c.P = P, c.worst = want_worst;
+    int ids[kMaxDims];
+    for (int i = 0; i < M; ++i) ids[i] = i;
+    do {  // lexicographic permutations; index 0 is the natural layout
+        Layout L;
+        L.M = M;
+        std::memcpy(L.axis, ids, sizeof(int) * M);
+        c.perms.push_back(L);
+    } while (std::next_permutation(ids, ids + M));
+    c.F = (int)c.perms.size();
+    c.masks = 1 << M;
+    c.pair.assign((size_t)c.F * c.F, -1);
+    c.memo.assign((size_t)M * c.F * c.masks, INT64_MIN);
+
+    unsigned mask = 1u << (M - 1);
+    total = c.solve(0, 0, mask);
+    order.clear();
+    order.push_back(c.perms[0]);
+    int f = 0;
+    for (int layer = 0; layer + 1 < M; ++layer) {
+        int64_t want = c.solve(layer, f, mask);
+        for (int g = 0; g < c.F; ++g) {
+            int last = c.perms[g].axis[M - 1];
+            if (mask & (1u << last)) continue;
+            if (c.amount(f, g) + c.solve(layer + 1, g, mask | (1u << last)) == want) {
+                order.push_back(c.perms[g]);
+                f = g;
+                mask |= 1u << last;
+                break;
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace planner
+}  // namespace mdfft

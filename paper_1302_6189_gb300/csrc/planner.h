@@ -1,0 +1,64 @@
+// planner.h -- host-side row-wise decomposition planner (integer maths only).
+//
+// Layouts are permutations of axis ids listed slowest -> fastest.  The
+// chunks of a layout are the f_MD chunks (Sec. 3.2) of the dims permuted into
+// that layout.  Amounts are in data points.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace mdfft {
+namespace planner {
+
+constexpr int kMaxDims = 8;
+
+struct Layout {
+    int M = 0;
+    int axis[kMaxDims] = {0};
+};
+
+// Number of leading dims the chunks are cut on (smallest k with
+// P <= d_0 ... d_{k-1}); -1 if P < 1 or P > product(d).
+int regime(int M, const int64_t *d, int64_t P);
+
+// f_MD of Sec. 3.2 over dims d (already in layout order); pid in [0, P].
+int64_t fmd(int M, const int64_t *d, int64_t P, int64_t pid);
+
+// Mixed-radix digits of x over dims d.
+void digits(int M, const int64_t *d, int64_t x, int64_t *c);
+
+// Dims of N permuted into layout L.
+void layout_dims(const Layout &L, const int64_t *N, int64_t *d);
+
+// Half-open axis-aligned box in natural axis coordinates.
+struct Box {
+    int64_t lo[kMaxDims];
+    int64_t hi[kMaxDims];
+};
+
+// Boxes (natural coordinates) covering layout-L row-major indices [a, b).
+void range_boxes(const Layout &L, const int64_t *N, int64_t a, int64_t b, std::vector<Box> &out);
+
+// Points whose owner differs between the chunks of layouts A and B.
+int64_t transition_amount(int M, const int64_t *N, int64_t P, const Layout &A, const Layout &B);
+
+// Split-line amount of layout L: sum over lines along its last axis of
+// N_axis * (owners - 1).
+int64_t split_line_amount(int M, const int64_t *N, int64_t P, const Layout &L);
+
+// Owner of row-major index x of layout L (closed form inverse of f_MD).
+int64_t owner_of(int M, const int64_t *N, int64_t P, const Layout &L, int64_t x);
+
+// Validates an order of M layouts: first natural, each a permutation, last
+// axes all distinct.  Returns "" or a message.
+std::string check_order(int M, const std::vector<Layout> &order);
+
+// Dynamic-programming order search (M <= 6).  want_worst selects max.
+// Ties: lexicographically smallest sequence of layouts.
+bool search_order(int M, const int64_t *N, int64_t P, bool want_worst, std::vector<Layout> &order,
+                  int64_t &total, std::string &err);
+
+}  // namespace planner
+}  // namespace mdfft

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libmdfft (include/mdfft.h).
+
+Argument marshalling only: every function here converts Python arguments to
+the C types of the function of the same name and raises ``MdfftError`` on a
+non-zero status.  All computation happens in the library (host planner and
+sm_103a kernels).  ``Plan`` is a convenience wrapper that passes torch CUDA
+tensors' data pointers and the current CUDA stream.
+
+The library must have been built (``__graft_entry__.build()``); importing this
+module without it raises ImportError -- there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libmdfft.so")
+AXES = "abcdefgh"
+MAX_DIMS = 8
+
+MDFFT_OK, MDFFT_E_ARG, MDFFT_E_ORDER, MDFFT_E_RANGE = 0, -1, -2, -3
+MDFFT_E_NOMEM, MDFFT_E_CUDA, MDFFT_E_TIMEOUT, MDFFT_E_UNSUPPORTED = -4, -5, -6, -7
+MDFFT_C64, MDFFT_C128, MDFFT_C64_TC_FP16, MDFFT_C64_TC_BF16 = 0, 1, 2, 3
+MDFFT_PLAN_HOST_ONLY, MDFFT_PLAN_INPLACE = 0x1, 0x2
+DTYPES = {"c64": MDFFT_C64, "c128": MDFFT_C128, "c64_tc_fp16": MDFFT_C64_TC_FP16,
+          "c64_tc_bf16": MDFFT_C64_TC_BF16}
+STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_ORDER", -3: "E_RANGE", -4: "E_NOMEM", -5: "E_CUDA",
+                -6: "E_TIMEOUT", -7: "E_UNSUPPORTED"}
+
+i64, c_int, c_void_p, c_size_t = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+P_ = ctypes.POINTER
+
+
+class MdfftComm(ctypes.Structure):
+    _fields_ = [("per_transition", i64 * MAX_DIMS), ("total", i64), ("final_to_natural", i64),
+                ("split_line", i64 * MAX_DIMS), ("paper_total", i64), ("regime", c_int * MAX_DIMS),
+                ("amount_slab", ctypes.c_double), ("amount_pencil", ctypes.c_double),
+                ("amount_volumetric", ctypes.c_double)]
+
+
+class MdfftPassInfo(ctypes.Structure):
+    _fields_ = [("line_length", i64), ("tile_g", c_int), ("tile_h", c_int), ("threads", c_int),
+                ("smem_bytes", c_int), ("ctas", i64), ("fft_axis", c_int), ("store_axis", c_int)]
+
+
+SIGNATURES = {
+    "mdfft_plan": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint]),
+    "mdfft_exec": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "mdfft_exec_counted": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "mdfft_comm_volume": (c_int, [c_void_p, P_(MdfftComm)]),
+    "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
+    "mdfft_plan_order": (c_int, [c_void_p, P_(c_int)]),
+    "mdfft_order_search": (c_int, [c_int, P_(i64), i64, c_int, P_(c_int), P_(i64)]),
+    "mdfft_pass_timing": (c_int, [c_void_p, c_int]),
+    "mdfft_pass_times": (c_int, [c_void_p, P_(ctypes.c_float), c_int, P_(c_int)]),
+    "mdfft_exec_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "mdfft_pass_describe": (c_int, [c_void_p, c_int, P_(MdfftPassInfo)]),
+    "mdfft_workspace_size": (c_int, [c_void_p, P_(c_size_t)]),
+    "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
+    "mdfft_supported_length": (c_int, [i64, c_int]),
+    "mdfft_destroy": (c_int, [c_void_p]),
+    "mdfft_last_error": (ctypes.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is not built; run __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _LIB_PATH
+
+
+class MdfftError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.mdfft_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(st, where):
+    if st != MDFFT_OK:
+        raise MdfftError(st, where)
+
+
+def parse_order(order, M):
+    """'abc->cab->cba' or [[0,1,2],...] -> flat list of M*M axis ids."""
+    if isinstance(order, str):
+        layouts = [p.strip() for p in order.replace("→", "->").split("->")]
+        flat = [AXES.index(ch) for L in layouts for ch in L]
+    else:
+        flat = [int(a) for L in order for a in L]
+    if len(flat) != M * M:
+        raise ValueError(f"order must have {M} layouts of {M} axes")
+    return flat
+
+
+def format_order(order, M):
+    flat = parse_order(order, M)
+    return "->".join("".join(AXES[a] for a in flat[s * M:(s + 1) * M]) for s in range(M))
+
+
+def _dims(N):
+    return (i64 * len(N))(*[int(n) for n in N]), len(N)
+
+
+# ------------------------------------------------------------------- C entry points
+
+def mdfft_plan(N, P, order=None, dtype=MDFFT_C64, flags=0):
+    dims, M = _dims(N)
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    oarr = None if order is None else (c_int * (M * M))(*parse_order(order, M))
+    h = c_void_p()
+    _check(_lib.mdfft_plan(ctypes.byref(h), M, dims, int(P), oarr, dt, int(flags)), "mdfft_plan")
+    return h
+
+
+def mdfft_exec(plan, in_ptr, out_ptr, dir=-1, normalize=0, stream=0):
+    _check(_lib.mdfft_exec(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(dir), int(normalize),
+                           c_void_p(stream)), "mdfft_exec")
+
+
+def mdfft_exec_counted(plan, in_ptr, out_ptr, dir, normalize, stream, counts_ptr):
+    _check(_lib.mdfft_exec_counted(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(dir), int(normalize),
+                                   c_void_p(stream), c_void_p(counts_ptr)), "mdfft_exec_counted")
+
+
+def mdfft_comm_volume(plan, M):
+    c = MdfftComm()
+    _check(_lib.mdfft_comm_volume(plan, ctypes.byref(c)), "mdfft_comm_volume")
+    return {"per_transition": list(c.per_transition[: M - 1]), "total": c.total,
+            "final_to_natural": c.final_to_natural, "split_line": list(c.split_line[:M]),
+            "paper_total": c.paper_total, "regime": list(c.regime[:M]),
+            "amount_slab": c.amount_slab, "amount_pencil": c.amount_pencil,
+            "amount_volumetric": c.amount_volumetric}
+
+
+def mdfft_chunk(plan, step, pid, M):
+    xs, xe = i64(), i64()
+    cs, ce = (i64 * M)(), (i64 * M)()
+    _check(_lib.mdfft_chunk(plan, int(step), int(pid), ctypes.byref(xs), ctypes.byref(xe), cs, ce),
+           "mdfft_chunk")
+    return xs.value, xe.value, list(cs), list(ce)
+
+
+def mdfft_plan_order(plan, M):
+    arr = (c_int * (M * M))()
+    _check(_lib.mdfft_plan_order(plan, arr), "mdfft_plan_order")
+    return [list(arr[s * M:(s + 1) * M]) for s in range(M)]
+
+
+def mdfft_order_search(N, P, want_worst=0):
+    dims, M = _dims(N)
+    arr = (c_int * (M * M))()
+    tot = i64()
+    _check(_lib.mdfft_order_search(M, dims, int(P), int(want_worst), arr, ctypes.byref(tot)),
+           "mdfft_order_search")
+    return [list(arr[s * M:(s + 1) * M]) for s in range(M)], tot.value
+
+
+def mdfft_pass_timing(plan, enable):
+    _check(_lib.mdfft_pass_timing(plan, int(enable)), "mdfft_pass_timing")
+
+
+def mdfft_pass_times(plan, M):
+    """(mean ms per pass, number of executions averaged)."""
+    arr = (ctypes.c_float * M)()
+    n = c_int()
+    _check(_lib.mdfft_pass_times(plan, arr, M, ctypes.byref(n)), "mdfft_pass_times")
+    return list(arr), n.value
+
+
+def mdfft_exec_host(plan, in_host_ptr, out_host_ptr, dev_in_ptr, dev_out_ptr, dir=-1, normalize=0, stream=0):
+    _check(_lib.mdfft_exec_host(plan, c_void_p(in_host_ptr), c_void_p(out_host_ptr), c_void_p(dev_in_ptr),
+                                c_void_p(dev_out_ptr), int(dir), int(normalize), c_void_p(stream)),
+           "mdfft_exec_host")
+
+
+def mdfft_pass_describe(plan, s):
+    info = MdfftPassInfo()
+    _check(_lib.mdfft_pass_describe(plan, int(s), ctypes.byref(info)), "mdfft_pass_describe")
+    return {f: getattr(info, f) for f, _ in MdfftPassInfo._fields_}
+
+
+def mdfft_workspace_size(plan):
+    n = c_size_t()
+    _check(_lib.mdfft_workspace_size(plan, ctypes.byref(n)), "mdfft_workspace_size")
+    return n.value
+
+
+def mdfft_launches_per_exec(plan):
+    n = c_int()
+    _check(_lib.mdfft_launches_per_exec(plan, ctypes.byref(n)), "mdfft_launches_per_exec")
+    return n.value
+
+
+def mdfft_supported_length(n, dtype=MDFFT_C64):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return bool(_lib.mdfft_supported_length(int(n), dt))
+
+
+def mdfft_destroy(plan):
+    _check(_lib.mdfft_destroy(plan), "mdfft_destroy")
+
+
+def mdfft_last_error():
+    return _lib.mdfft_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------- torch convenience
+
+_TORCH_DTYPE = {MDFFT_C64: "complex64", MDFFT_C128: "complex128",
+                MDFFT_C64_TC_FP16: "complex64", MDFFT_C64_TC_BF16: "complex64"}
+
+
+class Plan:
+    """A plan bound to torch CUDA tensors: ``Plan(shape, P, order, dtype)``."""
+
+    def __init__(self, shape, P, order=None, dtype="c64", flags=0):
+        self.shape = tuple(int(n) for n in shape)
+        self.M = len(self.shape)
+        self.P = int(P)
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.flags = int(flags)
+        self.handle = mdfft_plan(self.shape, P, order, self.dtype, flags)
+
+    def _stream(self, stream):
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        return s.cuda_stream
+
+    def _check_tensor(self, t, name):
+        import torch
+        want = getattr(torch, _TORCH_DTYPE[self.dtype])
+        if not (t.is_cuda and t.dtype == want and t.is_contiguous() and tuple(t.shape) == self.shape):
+            raise ValueError(f"{name} must be a contiguous CUDA {want} tensor of shape {self.shape}")
+
+    def exec(self, x, out=None, dir=-1, normalize=False, stream=None):
+        import torch
+        self._check_tensor(x, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "out")
+        mdfft_exec(self.handle, x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
+        return out
+
+    def exec_counted(self, x, out=None, dir=-1, normalize=False, stream=None):
+        """Returns (out, counts): counts is an int64 CUDA tensor of 2*M entries."""
+        import torch
+        self._check_tensor(x, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "out")
+        counts = torch.empty(2 * self.M, dtype=torch.int64, device=x.device)
+        mdfft_exec_counted(self.handle, x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)),
+                           self._stream(stream), counts.data_ptr())
+        return out, counts
+
+    def comm_volume(self):
+        return mdfft_comm_volume(self.handle, self.M)
+
+    def order(self):
+        return mdfft_plan_order(self.handle, self.M)
+
+    def order_str(self):
+        return format_order(self.order(), self.M)
+
+    def chunk(self, step, pid):
+        return mdfft_chunk(self.handle, step, pid, self.M)
+
+    def describe(self):
+        return [mdfft_pass_describe(self.handle, s) for s in range(self.M)]
+
+    def set_timing(self, enable=True):
+        mdfft_pass_timing(self.handle, enable)
+
+    def pass_times(self):
+        """(mean ms per pass over the recorded executions, how many)."""
+        return mdfft_pass_times(self.handle, self.M)
+
+    def exec_host(self, x_host, out_host, dev_in, dev_out, dir=-1, normalize=False, stream=None):
+        """End to end on host tensors (pinned for async copies) via caller device buffers."""
+        for t, name in ((dev_in, "dev_in"), (dev_out, "dev_out")):
+            self._check_tensor(t, name)
+        mdfft_exec_host(self.handle, x_host.data_ptr(), out_host.data_ptr(), dev_in.data_ptr(),
+                        dev_out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
+        return out_host
+
+    def workspace_bytes(self):
+        return mdfft_workspace_size(self.handle)
+
+    def launches(self):
+        return mdfft_launches_per_exec(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            mdfft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

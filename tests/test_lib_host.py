@@ -1,0 +1,155 @@
+"""The C-ABI library on the host: it loads, exports every entry point the
+header declares, and its planner (box intersection, dynamic-programming
+order search) matches the oracle (owner arrays, exhaustive enumeration)
+bit for bit.  No GPU: plans are made with MDFFT_PLAN_HOST_ONLY."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1302_6189_gb300 as md
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HOST = md.MDFFT_PLAN_HOST_ONLY
+
+
+def test_library_exports_every_declared_symbol():
+    with open(os.path.join(ROOT, "include", "mdfft.h")) as f:
+        header = f.read()
+    declared = set(re.findall(r"\b(mdfft_[a-z_0-9]+)\s*\(", header))
+    assert len(declared) >= 15
+    lib = ctypes.CDLL(md.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(md.mdfft.SIGNATURES)
+
+
+def _plan(N, P, order=None):
+    return md.mdfft_plan(N, P, order, "c64", HOST)
+
+
+def _cv(N, P, order):
+    h = _plan(N, P, order)
+    try:
+        return md.mdfft_comm_volume(h, len(N))
+    finally:
+        md.mdfft_destroy(h)
+
+
+ORDERS3 = [oracle.format_order(o) for o in oracle.enumerate_orders(3)]
+
+
+@pytest.mark.parametrize("N", [(4, 5, 6), (8, 8, 8), (6, 3, 10), (16, 4, 9)])
+def test_comm_volume_matches_oracle_every_3d_order(N):
+    T = int(np.prod(N))
+    Ps = sorted({1, 2, 3, N[0], N[0] + 1, N[0] * N[1], N[0] * N[1] + 1, T // 3, T - 1, T})
+    for order in ORDERS3:
+        for P in Ps:
+            got, ref = _cv(N, P, order), oracle.comm_volume(N, P, order)
+            for key in ("per_transition", "total", "final_to_natural", "split_line", "paper_total"):
+                assert got[key] == ref[key], (order, P, key)
+
+
+def test_comm_volume_matches_oracle_4d_5d():
+    rng = np.random.default_rng(44)
+    for M in (4, 5):
+        orders = oracle.enumerate_orders(M, cap=5000)
+        for _ in range(12):
+            N = tuple(int(v) for v in rng.integers(2, 6, size=M))
+            T = int(np.prod(N))
+            P = int(rng.integers(1, T + 1))
+            o = orders[rng.integers(0, len(orders))]
+            got, ref = _cv(N, P, o), oracle.comm_volume(N, P, o)
+            assert got["per_transition"] == ref["per_transition"]
+            assert got["final_to_natural"] == ref["final_to_natural"]
+            assert got["split_line"] == ref["split_line"]
+
+
+def test_regimes_and_closed_forms():
+    got = _cv((64, 64, 64), 8192, "abc->acb->bca")
+    assert got["regime"] == [3, 3, 3]
+    assert got["amount_slab"] == pytest.approx(oracle.amount_slab(64, 8192))
+    assert got["amount_pencil"] == pytest.approx(oracle.amount_pencil(64, 8192))
+    assert got["amount_volumetric"] == pytest.approx(oracle.amount_volumetric(3, 64, 8192))
+    # BASELINE labels 256^3 at P = 16, 256, 4096 as three regimes; f_3D gives 1, 1, 2
+    for P, k in ((16, 1), (256, 1), (4096, 2), (131072, 3)):
+        assert _cv((256, 256, 256), P, "abc->cab->cba")["regime"][0] == k
+
+
+@pytest.mark.parametrize("N,P", [((4, 6, 5), 7), ((8, 8, 8), 16), ((3, 4, 2, 5), 11), ((2, 3, 2, 3, 2), 9)])
+def test_chunks_match_oracle_in_every_layout(N, P):
+    M = len(N)
+    h = _plan(N, P)
+    try:
+        order = md.mdfft_plan_order(h, M)
+        for step in range(M + 1):
+            L = order[step] if step < M else list(range(M))
+            Nl = [N[a] for a in L]
+            for pid in range(P):
+                assert md.mdfft_chunk(h, step, pid, M) == oracle.chunk(Nl, P, pid)
+    finally:
+        md.mdfft_destroy(h)
+
+
+@pytest.mark.parametrize("N,Ps", [((8, 8, 8), (2, 8, 16, 40, 64, 100, 512)),
+                                  ((6, 4, 5), (3, 6, 7, 24, 25, 120)),
+                                  ((4, 4, 4, 4), (2, 4, 16, 32, 64, 200)),
+                                  ((3, 4, 2, 3), (5, 12, 13, 30)),
+                                  ((3, 3, 3, 3, 3), (2, 9, 27, 81, 100))])
+def test_order_search_matches_exhaustive_oracle(N, Ps):
+    for P in Ps:
+        ref = oracle.order_search(N, P, best_cap=1)
+        best_order, best = md.mdfft_order_search(N, P, 0)
+        worst_order, worst = md.mdfft_order_search(N, P, 1)
+        assert (best, worst) == (ref["best"], ref["worst"])
+        assert best_order == ref["best_order"]      # same tie-break: lexicographically first
+        assert worst_order == ref["worst_order"]
+        # a plan made without an order uses the best one
+        h = _plan(N, P)
+        try:
+            assert md.mdfft_plan_order(h, len(N)) == ref["best_order"]
+        finally:
+            md.mdfft_destroy(h)
+
+
+def test_errors_are_status_codes():
+    with pytest.raises(md.MdfftError) as e:
+        _plan((8, 8, 8), 16, "acb->cab->cba")
+    assert e.value.status == -2
+    with pytest.raises(md.MdfftError) as e:
+        _plan((8, 8, 8), 16, "abc->cab->cab")
+    assert e.value.status == -2
+    with pytest.raises(md.MdfftError) as e:
+        _plan((2, 2, 2), 9)
+    assert e.value.status == -3
+    with pytest.raises(md.MdfftError) as e:
+        _plan((2, 2, 2), 0)
+    assert e.value.status == -3
+    with pytest.raises(md.MdfftError) as e:
+        md.mdfft_plan((8,), 2, None, "c64", HOST)
+    assert e.value.status == -7
+    with pytest.raises(md.MdfftError) as e:
+        md.mdfft_plan((8, 0, 8), 2, None, "c64", HOST)
+    assert e.value.status == -1
+    h = _plan((8, 8, 8), 4)
+    try:
+        with pytest.raises(md.MdfftError) as e:
+            md.mdfft_exec(h, 16, 32, -1, 0, 0)        # host-only plans never launch
+        assert e.value.status == -1
+        with pytest.raises(md.MdfftError):
+            md.mdfft_chunk(h, 4, 0, 3)
+        with pytest.raises(md.MdfftError):
+            md.mdfft_chunk(h, 0, 4, 3)
+    finally:
+        md.mdfft_destroy(h)
+
+
+def test_supported_lengths():
+    for n in (1, 2, 3, 5, 24, 48, 64, 96, 160, 192, 256, 512, 1024):
+        assert md.mdfft_supported_length(n, "c64") and md.mdfft_supported_length(n, "c128")
+    for n in (7, 11, 2048, 0, -4):
+        assert not md.mdfft_supported_length(n, "c64")

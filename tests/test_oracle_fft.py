@@ -18,6 +18,17 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def test_dft_point_matches_numpy_and_naive():
+    rng = np.random.default_rng(3)
+    for shape in [(6, 5, 8), (4, 3, 5, 2), (24, 20, 16)]:
+        x = si.uniform_complex(shape, 31)
+        ref = np.fft.fftn(x)
+        for _ in range(6):
+            k = tuple(int(rng.integers(0, n)) for n in shape)
+            assert abs(oracle.dft_point(x, k) - ref[k]) < 1e-12 * np.abs(ref).max()
+            assert abs(oracle.dft_point(x, k, sign=+1) - x.size * np.fft.ifftn(x)[k]) < 1e-12 * np.abs(ref).max()
+
+
 def test_naive_dft_matches_numpy():
     # numpy's pocketfft is a library routine independent of the oracle.
     for shape in TINY:
