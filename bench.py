@@ -46,13 +46,16 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_1302_6189_gb300", "csrc", f) for f i
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--P", type=int, default=P_DEFAULT)
     ap.add_argument("--no-extra", action="store_true", help="skip the per-order / complex128 table")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one warm-up and one profiled forward transform of one 256^3 complex64 volume "
+                         "(3 + 3 pass launches), for ncu captures")
     return ap.parse_args()
 
 
@@ -95,7 +98,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -112,7 +115,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.f,
+                                          "-lms", "20", "-i", str(self.gpu)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -212,7 +215,8 @@ def oracle_fwd_inv_seconds(shape, reps, nthreads):
 
 def cpu_baseline(shape, elem):
     nthreads = len(os.sched_getaffinity(0))
-    reps = 2
+    # about 20 s of CPU work: one forward + inverse takes ~0.25 s on 16 cores
+    reps = max(2, min(12, int(round(80 / max(1, nthreads)))))
     times = oracle_fwd_inv_seconds(shape, reps, nthreads)
     per_step, _ = algorithmic_bytes(shape, elem)
     gbs = 2 * per_step * reps / sum(times) / 1e9
@@ -427,8 +431,29 @@ def extra_table(dev, x, P):
     return res
 
 
+def profile_case(args):
+    import numpy as np
+    import torch
+
+    import synth_inputs as si
+    from paper_1302_6189_gb300 import Plan
+
+    torch.cuda.set_device(0)
+    x = torch.from_numpy(si.uniform_complex(SHAPE, si.SEEDS["cube256"], np.complex64)).cuda()
+    with Plan(SHAPE, args.P, None, "c64") as plan:
+        y = torch.empty_like(x)
+        plan.exec(x, y)  # warm-up: launches 1-3
+        plan.exec(x, y)  # profiled: launches 4-6
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "256^3 c64 forward", "order": plan.order_str(),
+                          "passes": plan.describe()}))
+
+
 def main():
     args = parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
