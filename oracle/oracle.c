@@ -359,9 +359,10 @@ static int layout_ok(int M, const int *L) {
 /* ------------------------------------------------------------------------ */
 /* 5. Owners and communication amounts by brute force.                       */
 /*    A layout's chunks are the f_MD chunks of its row-major order, i.e. of  */
-/*    the dims permuted into that layout ("derived in the same way", Sec.   */
-/*    3.1).  The amount of one transpose is the number of points whose owner */
-/*    changes; the rest is reused in place (Sec. 1, Sec. 3.1 on Fig. 2).     */
+/*    the dims permuted into that layout (Sec. 3.1: other layouts follow    */
+/*    by the same construction).  The amount of one transpose is the number  */
+/*    of points whose owner changes; the rest is reused in place (Sec. 1,    */
+/*    Sec. 3.1 on Fig. 2).                                                   */
 /* ------------------------------------------------------------------------ */
 
 /* owner[natural linear index] = rank holding that point in layout L. */
