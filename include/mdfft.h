@@ -208,6 +208,40 @@ int mdfft_supported_length(int64_t n, mdfft_dtype dt);
 
 mdfft_status mdfft_destroy(mdfft_plan_t plan);
 
+/*
+ * mdfft_exec_noalloc -- the transform of mdfft_plan + mdfft_exec, for callers
+ * that cannot let a library allocate GPU memory: applications whose device
+ * memory is owned by their own allocator or memory pool, and loops where the
+ * device-wide synchronisation that cudaMalloc and cudaFree may cause is not
+ * acceptable.  The paper has no counterpart to this entry point; it is a
+ * property of this library's interface only.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree or any other device allocator
+ * (torch's included), and no host heap memory on success.  Its scratch -- the
+ * twiddle tables and the array the passes ping-pong through -- is one static
+ * device array of MDFFT_NOALLOC_SCRATCH_BYTES that every GPU which loads the
+ * library holds until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call on each device before any stream capture.
+ *   M, N, dt, dir, normalize  as for mdfft_plan / mdfft_exec.
+ *   order     M*M axis ids as for mdfft_plan; required (NULL is E_ARG) --
+ *             get the best order from mdfft_order_search beforehand.
+ *   in, out   caller-owned device arrays of N_1 ... N_M elements; they must not
+ *             overlap (no in-place); in is not modified.
+ * Limits: N_1 ... N_M * element size <= MDFFT_NOALLOC_MAX_ARRAY_BYTES, else
+ * E_UNSUPPORTED with a message.  The virtual process count of mdfft_plan is
+ * not an argument: it changes no result.
+ * Every call shares the one scratch array and leaves its contents behind;
+ * nothing in it needs to start at zero (each call writes every scratch byte
+ * it reads before reading it).  Calls that can overlap on the GPU -- on
+ * different streams, or from different host threads, on one device -- race on
+ * the scratch and give wrong results: serialise them.
+ */
+#define MDFFT_NOALLOC_SCRATCH_BYTES (64ull << 20)
+#define MDFFT_NOALLOC_MAX_ARRAY_BYTES (MDFFT_NOALLOC_SCRATCH_BYTES - (256ull << 10))
+mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *order, mdfft_dtype dt, const void *in_dev,
+                                void *out_dev, int dir, int normalize, mdfft_stream_t stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *mdfft_last_error(void);
 

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -555,3 +556,175 @@ mdfft_status mdfft_destroy(mdfft_plan_t p) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mdfft_exec_noalloc: the transform without any device allocation.
+//
+// The scratch it needs (twiddle tables and the array the passes ping-pong
+// through) is this file-scope device array.  Every GPU that loads the library
+// holds it until the process exits.  Host code must not use the symbol's
+// address directly (on the host it names a stand-in); the device address is
+// taken once per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MDFFT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr size_t kNoallocTwiddleBytes = 256 * 1024;  // M tables of at most 1024 x 16 bytes
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+
+mdfft_status noalloc_fail(mdfft_status st, const char *msg) {
+    g_err = msg;  // the message is recorded like every other entry point's
+    return st;
+}
+
+// Device address of the scratch array on the current device (looked up once).
+mdfft_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) return noalloc_fail(MDFFT_E_UNSUPPORTED, "device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_noalloc_addr[dev];
+    return MDFFT_OK;
+}
+
+// Pass s of the order held in the fixed-size array L (no heap use): the same
+// launch configuration mdfft_plan builds, without the owner maps of the
+// count mode.
+mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dtype dt, size_t elem, int s,
+                          Pass &ps) {
+    pl::Layout nat;
+    nat.M = M;
+    for (int i = 0; i < M; ++i) nat.axis[i] = i;
+    const pl::Layout &Li = L[s];
+    const pl::Layout &Lo = (s + 1 < M) ? L[s + 1] : nat;
+    ps.f = Li.axis[M - 1];
+    ps.g = Lo.axis[M - 1];
+    ps.h = -1;
+    for (int i = M - 2; i >= 0; --i)
+        if (Lo.axis[i] != ps.f) {
+            ps.h = Lo.axis[i];
+            break;
+        }
+    ps.n = N[ps.f];
+    if (!lookup(dt, ps.n, &ps.k)) return noalloc_fail(MDFFT_E_UNSUPPORTED, "a line length is not built for this dtype");
+    int64_t sin_[pl::kMaxDims], sout[pl::kMaxDims];
+    layout_strides(Li, N, sin_);
+    layout_strides(Lo, N, sout);
+    PassArgs &a = ps.args;
+    std::memset(&a, 0, sizeof(a));
+    const int64_t Ng = N[ps.g], Nh = ps.h >= 0 ? N[ps.h] : 1;
+    int Bg = 1, Bh = 1;
+    choose_tile(ps.k.lines, Ng, Nh, elem, &Bg, &Bh);
+    a.Bg = Bg, a.Bh = Bh, a.Ng = Ng, a.Nh = Nh;
+    a.gblocks = (Ng + Bg - 1) / Bg;
+    a.hblocks = (Nh + Bh - 1) / Bh;
+    a.in_sg = sin_[ps.g];
+    a.in_sh = ps.h >= 0 ? sin_[ps.h] : 0;
+    a.out_sh = ps.h >= 0 ? sout[ps.h] : 0;
+    a.out_sf = sout[ps.f];
+    ps.ctas = a.gblocks * a.hblocks;
+    for (int i = M - 1; i >= 0; --i) {
+        int ax = Lo.axis[i];
+        if (ax == ps.f || ax == ps.g || ax == ps.h) continue;
+        a.rest_count[a.nrest] = N[ax];
+        a.rest_in[a.nrest] = sin_[ax];
+        a.rest_out[a.nrest] = sout[ax];
+        a.nrest++;
+        ps.ctas *= N[ax];
+    }
+    a.scale = 1.0;
+    return MDFFT_OK;
+}
+
+}  // namespace
+
+extern "C" mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *order, mdfft_dtype dt,
+                                           const void *in, void *out, int dir, int normalize,
+                                           mdfft_stream_t stream) {
+    if (!N || !order || !in || !out) return noalloc_fail(MDFFT_E_ARG, "null argument (the order is required)");
+    if (M < 2 || M > MDFFT_MAX_DIMS) return noalloc_fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
+    if (dt != MDFFT_C64 && dt != MDFFT_C128) return noalloc_fail(MDFFT_E_UNSUPPORTED, "dtype must be C64 or C128");
+    if (dir != -1 && dir != 1) return noalloc_fail(MDFFT_E_ARG, "dir must be -1 (forward) or +1 (inverse)");
+    if (normalize != 0 && !(normalize == 1 && dir == 1))
+        return noalloc_fail(MDFFT_E_ARG, "normalize = 1 is only defined for the inverse");
+    const size_t elem = dt == MDFFT_C128 ? 16 : 8;
+    unsigned __int128 T = 1;
+    for (int i = 0; i < M; ++i) {
+        if (N[i] < 1) return noalloc_fail(MDFFT_E_ARG, "dims must be >= 1");
+        T *= (unsigned __int128)N[i];
+    }
+    if (T * elem > (unsigned __int128)MDFFT_NOALLOC_MAX_ARRAY_BYTES)
+        return noalloc_fail(MDFFT_E_UNSUPPORTED,
+                            "array larger than MDFFT_NOALLOC_MAX_ARRAY_BYTES; use mdfft_plan + mdfft_exec");
+    const size_t bytes = (size_t)T * elem;
+    if ((uintptr_t)in % elem || (uintptr_t)out % elem) return noalloc_fail(MDFFT_E_ARG, "misaligned data pointer");
+    if (overlaps(in, out, bytes)) return noalloc_fail(MDFFT_E_ARG, "in and out must not overlap");
+    // the order, validated without heap use
+    pl::Layout L[MDFFT_MAX_DIMS];
+    unsigned used_last = 0;
+    for (int s = 0; s < M; ++s) {
+        L[s].M = M;
+        unsigned seen = 0;
+        for (int i = 0; i < M; ++i) {
+            int a = order[s * M + i];
+            if (a < 0 || a >= M || (seen & (1u << a))) return noalloc_fail(MDFFT_E_ORDER, "a layout is not a permutation");
+            if (s == 0 && a != i) return noalloc_fail(MDFFT_E_ORDER, "layout 0 must be the natural order");
+            seen |= 1u << a;
+            L[s].axis[i] = a;
+        }
+        unsigned last = 1u << L[s].axis[M - 1];
+        if (used_last & last) return noalloc_fail(MDFFT_E_ORDER, "a layout transforms an axis twice");
+        used_last |= last;
+    }
+    Pass pass[MDFFT_MAX_DIMS];
+    for (int s = 0; s < M; ++s) {
+        mdfft_status st = noalloc_pass(M, N, L, dt, elem, s, pass[s]);
+        if (st != MDFFT_OK) return st;
+    }
+    unsigned char *scratch = nullptr;
+    mdfft_status st = noalloc_scratch(&scratch);
+    if (st != MDFFT_OK) return st;
+    unsigned char *ws = scratch + kNoallocTwiddleBytes;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    // twiddles of every pass, rewritten by every call in stream order
+    for (int s = 0; s < M; ++s) {
+        const int64_t n = pass[s].n;
+        twiddle_kernel<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(scratch + (size_t)s * 1024 * elem, n,
+                                                                   dt == MDFFT_C128);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle launch");
+    void *dst[MDFFT_MAX_DIMS];
+    dst[M - 1] = out;
+    for (int s = M - 2; s >= 0; --s) dst[s] = (dst[s + 1] == out) ? (void *)ws : out;
+    const void *src = in;
+    for (int s = 0; s < M; ++s) {
+        const PassKernel &k = pass[s].k;
+        if (k.smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        }
+        PassArgs a = pass[s].args;
+        a.in = src;
+        a.out = dst[s];
+        a.tw = scratch + (size_t)s * 1024 * elem;
+        a.conj = dir == 1;
+        a.scale = (s == M - 1 && normalize) ? 1.0 / (double)T : 1.0;
+        void *args[] = {&a};
+        e = cudaLaunchKernel(k.fn, dim3((unsigned)pass[s].ctas), dim3(k.threads), args, k.smem, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+        src = dst[s];
+    }
+    return MDFFT_OK;
+}

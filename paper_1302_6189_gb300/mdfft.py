@@ -60,6 +60,7 @@ SIGNATURES = {
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_supported_length": (c_int, [i64, c_int]),
     "mdfft_destroy": (c_int, [c_void_p]),
+    "mdfft_exec_noalloc": (c_int, [c_int, P_(i64), P_(c_int), c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_last_error": (ctypes.c_char_p, []),
 }
 
@@ -208,6 +209,15 @@ def mdfft_supported_length(n, dtype=MDFFT_C64):
 
 def mdfft_destroy(plan):
     _check(_lib.mdfft_destroy(plan), "mdfft_destroy")
+
+
+def mdfft_exec_noalloc(N, order, dtype, in_ptr, out_ptr, dir=-1, normalize=0, stream=0):
+    """The transform without any device allocation (scratch is a static device array)."""
+    dims, M = _dims(N)
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    oarr = None if order is None else (c_int * (M * M))(*parse_order(order, M))
+    _check(_lib.mdfft_exec_noalloc(M, dims, oarr, dt, c_void_p(in_ptr), c_void_p(out_ptr), int(dir),
+                                   int(normalize), c_void_p(stream)), "mdfft_exec_noalloc")
 
 
 def mdfft_last_error():
