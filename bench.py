@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--profile-case", action="store_true",
                     help="one warm-up and one profiled forward transform of one 256^3 complex64 volume "
                          "(3 + 3 pass launches), for ncu captures")
+    ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
     return ap.parse_args()
 
 
@@ -428,7 +429,44 @@ def extra_table(dev, x, P):
     res["c128"] = {"gbs": round(2 * per_transform / (ms * 1e-3) / 1e9, 1), "ms_per_transform": round(ms, 4),
                    "nominal_tflops_fp64": round(flops / (ms * 1e-3) / 1e12, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms]}
+    res["precision_512cubed"] = precision_study(dev)
     return res
+
+
+def precision_study(dev):
+    """512^3, N(0,1) re/im: FP32 SIMT vs tensor-core FP16 / BF16 hi-lo passes.
+    Throughput of the forward transform and its relative L2 error against the
+    complex128 (FP64) GPU path, which the parity tests tie to the CPU oracle."""
+    import numpy as np
+    import torch
+
+    import synth_inputs as si
+    from paper_1302_6189_gb300 import Plan, format_order
+
+    shape = (512, 512, 512)
+    per_transform, T = algorithmic_bytes(shape, 8)
+    x = torch.from_numpy(si.gaussian_complex(shape, si.SEEDS["precision512"], np.complex64)).to(dev)
+    with Plan(shape, 4096, None, "c128") as pl:
+        ref = pl.exec(x.to(torch.complex128))
+        order = pl.order()
+    out = {"order": format_order(order, 3), "reference": "complex128 GPU path", "dtypes": {}}
+    y = torch.empty_like(x)
+    for dt in ("c64", "c64_tc_fp16", "c64_tc_bf16"):
+        with Plan(shape, 4096, order, dt) as pl:
+            for _ in range(2):
+                pl.exec(x, y)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(5):
+                pl.exec(x, y)
+            b.record()
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / 5
+            err = float((torch.linalg.vector_norm(y.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref)).item())
+        out["dtypes"][dt] = {"gbs": round(per_transform / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4),
+                             "rel_l2_vs_fp64": err}
+    del ref
+    return out
 
 
 def profile_case(args):
@@ -439,13 +477,14 @@ def profile_case(args):
     from paper_1302_6189_gb300 import Plan
 
     torch.cuda.set_device(0)
-    x = torch.from_numpy(si.uniform_complex(SHAPE, si.SEEDS["cube256"], np.complex64)).cuda()
-    with Plan(SHAPE, args.P, None, "c64") as plan:
+    npdt = np.complex128 if args.profile_dtype == "c128" else np.complex64
+    x = torch.from_numpy(si.uniform_complex(SHAPE, si.SEEDS["cube256"], npdt)).cuda()
+    with Plan(SHAPE, args.P, None, args.profile_dtype) as plan:
         y = torch.empty_like(x)
         plan.exec(x, y)  # warm-up: launches 1-3
         plan.exec(x, y)  # profiled: launches 4-6
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": "256^3 c64 forward", "order": plan.order_str(),
+        print(json.dumps({"profile_case": f"256^3 {args.profile_dtype} forward", "order": plan.order_str(),
                           "passes": plan.describe()}))
 
 

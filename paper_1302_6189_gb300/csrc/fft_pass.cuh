@@ -40,7 +40,7 @@ struct OwnerMap {
 struct PassArgs {
     const void *in;
     void *out;
-    const void *tw;                 // N twiddles w_N^q, q < N, forward sign, pass precision
+    const void *tw;                 // twiddle table of the radix plan (tw_offset layout), pass precision
     int64_t gblocks, hblocks;       // tiles along g and along h
     int nrest;                      // remaining axes (not f, g, h), one tile unit each
     int64_t rest_count[kMaxTileDims];
@@ -71,7 +71,7 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
     while (n % 2 == 0) n /= 2, ++e;
     // powers of two: as few stages as radix 16 allows, balanced
     const int pw[11][3] = {{0, 0, 0},  {2, 0, 0},  {4, 0, 0},  {8, 0, 0},  {16, 0, 0}, {8, 4, 0},
-                           {8, 8, 0},  {16, 8, 0}, {16, 16, 0}, {8, 8, 8}, {16, 8, 8}};
+                           {8, 8, 0},  {16, 8, 0}, {16, 16, 0}, {16, 16, 2}, {16, 8, 8}};
     if (e <= 10)
         for (int i = 0; i < 3; ++i)
             if (pw[e][i]) p.R[p.S++] = pw[e][i];
@@ -82,33 +82,58 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
     return p;
 }
 
+// Twiddle table of a radix plan.  Stage 0 needs none (w^0 = 1); stage s >= 1,
+// after NS = R_0 ... R_{s-1} points are combined, uses w_{NS R}^{k r} for
+// k < NS, r < R, stored as entry r * NS + k (consecutive k are consecutive
+// words, so the lanes of a warp read distinct banks) at tw_offset(plan, s).
+__host__ __device__ constexpr int tw_offset(const RadixPlan &p, int s) {
+    int off = 0, ns = 1;
+    for (int i = 0; i < s && i < p.S; ++i) {
+        if (i > 0) off += ns * p.R[i];
+        ns *= p.R[i];
+    }
+    return off;
+}
+__host__ __device__ constexpr int tw_entries(const RadixPlan &p) { return tw_offset(p, p.S); }
+
 template <typename Real> struct Cx;
 template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };
 
-// Launch configuration of the pass kernel for line length N.
-template <typename Real, int N> struct PassCfg {
+__host__ __device__ constexpr RadixPlan radix_plan_tc(int n);
+
+// Launch configuration of the pass kernel for line length N.  TC != 0 selects
+// the tensor-core variant (complex64 only): radix-16 stages run as GEMMs.
+template <typename Real, int N, int TC = 0> struct PassCfg {
     using C = typename Cx<Real>::T;
-    static constexpr RadixPlan plan = radix_plan(N);
+    static_assert(TC == 0 || sizeof(Real) == 4, "tensor-core stages are complex64 only");
+    static constexpr RadixPlan plan = TC ? radix_plan_tc(N) : radix_plan(N);
     static_assert(plan.S >= 0, "unsupported line length");  // S = 0: N = 1, a pure redistribution
     static constexpr int TL = N / plan.maxR;  // threads per line
     static constexpr int kTileElems = sizeof(Real) == 4 ? 4096 : 2048;
-    // lines per tile: a power of two near kTileElems / N, at least 8, and a
-    // whole number of warps per CTA
+    // lines per tile: a power of two near kTileElems / N, at least enough for
+    // 128-byte store runs (16 complex64 / 8 complex128), and a whole number
+    // of warps per CTA
+    // (tensor-core CTAs stay at <= 512 threads: their stages need ~100 registers)
+    static constexpr int kMaxThreads = TC ? 512 : 1024;
     static constexpr int lines_for() {
-        int l = 8;
-        while (l < 256 && 2 * l * N <= kTileElems) l *= 2;
-        while ((TL * l) % 32 != 0) l *= 2;
+        int l = 128 / (int)sizeof(C);
+        while (l > 1 && TL * l > kMaxThreads) l /= 2;
+        while (l < 256 && 2 * l * N <= kTileElems && 2 * TL * l <= kMaxThreads) l *= 2;
+        while ((TL * l) % 32 != 0 && 2 * TL * l <= kMaxThreads) l *= 2;
         return l;
     }
     static constexpr int LINES = lines_for();
-    static_assert(TL * LINES <= 1024, "CTA too large");
+    static_assert(TL * LINES <= kMaxThreads && (TL * LINES) % 32 == 0, "CTA shape");
     static constexpr int THREADS = TL * LINES;
     static constexpr int PADN = N + N / 16 + 1;  // padded line stride in the stage buffer
     static constexpr int TROW = LINES + 1;       // padded row of the transposed tile
     static constexpr int DATA = LINES * PADN > N * TROW ? LINES * PADN : N * TROW;
-    static constexpr size_t SMEM = (size_t)(DATA + N) * sizeof(C) + (size_t)LINES * sizeof(int64_t);
-    static constexpr bool DIRECT = TL * (int)sizeof(C) >= 32;  // first stage loads from HBM directly
+    static constexpr int TWN = tw_entries(plan) > 0 ? tw_entries(plan) : 1;  // twiddle entries
+    static constexpr int BFRAG = TC ? 1024 * 4 / (int)sizeof(C) : 0;  // tensor-core B fragments (in C units)
+    static constexpr size_t SMEM = (size_t)(DATA + TWN + BFRAG) * sizeof(C) + (size_t)LINES * sizeof(int64_t);
+    // first stage loads from HBM directly (tensor-core stages read shared memory)
+    static constexpr bool DIRECT = TC == 0 && TL * (int)sizeof(C) >= 32;
 };
 
 // ------------------------------------------------------------------ complex helpers
@@ -216,6 +241,12 @@ template <int R, typename C> __device__ __forceinline__ void dft(C (&v)[R]) {
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
+}  // namespace mdfft
+
+#include "tc_stage.cuh"
+
+namespace mdfft {
+
 __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
     unsigned __int128 q = (unsigned __int128)(x / m.tail);
     return (int64_t)(((q + 1) * (unsigned __int128)m.P - 1) / (unsigned __int128)m.lead);
@@ -226,18 +257,30 @@ __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
 // One Stockham stage with radix R after NS points already combined.
 // Butterfly j (< N/R) reads x[j + r N/R], applies w_{NS R}^{(j mod NS) r},
 // does DFT_R and writes y[(j / NS) NS R + j mod NS + r NS].
-template <typename Real, int N, int SI, int NS> struct Stages {
-    using Cfg = PassCfg<Real, N>;
+template <typename Real, int N, int SI, int NS, int TC = 0> struct Stages {
+    using Cfg = PassCfg<Real, N, TC>;
     using C = typename Cfg::C;
     static constexpr int R = Cfg::plan.R[SI];
     static constexpr int NB = N / R;
     static constexpr int PER = (NB + Cfg::TL - 1) / Cfg::TL;
     static constexpr bool FIRST = SI == 0;
     static constexpr bool LAST = SI == Cfg::plan.S - 1;
+    static constexpr int TWOFF = tw_offset(Cfg::plan, SI);
 
     // gsrc: this thread's line in HBM (first stage, direct loads) or null
     __device__ __forceinline__ static void run(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
-                                               bool ok, bool conj) {
+                                               bool ok, bool conj, bool active) {
+        if constexpr (TC != 0 && R == 16) {
+            tc_radix16_stage<TC, N, Cfg::LINES, Cfg::THREADS, Cfg::PADN, Cfg::TROW, NS, LAST>(
+                buf, tile, tw + TWOFF, reinterpret_cast<const uint32_t *>(tw + Cfg::TWN), active);
+        } else {
+            simt(buf, tile, tw, gsrc, line, t, ok, conj);
+        }
+        if constexpr (!LAST) Stages<Real, N, SI + 1, NS * R, TC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active);
+    }
+
+    __device__ __forceinline__ static void simt(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
+                                                bool ok, bool conj) {
         C v[PER][R];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
@@ -265,7 +308,7 @@ template <typename Real, int N, int SI, int NS> struct Stages {
                 const int k = j % NS;
                 if constexpr (NS > 1) {
 #pragma unroll
-                    for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], tw[k * r * (N / (NS * R))]);
+                    for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], tw[TWOFF + r * NS + k]);
                 }
                 dft<R>(v[i]);
                 const int base = (j / NS) * NS * R + k;
@@ -280,28 +323,28 @@ template <typename Real, int N, int SI, int NS> struct Stages {
             }
         }
         __syncthreads();
-        if constexpr (!LAST) Stages<Real, N, SI + 1, NS * R>::run(buf, tile, tw, gsrc, line, t, ok, conj);
     }
 };
 
-// ------------------------------------------------------------------ the kernel
+// ------------------------------------------------------------------ one tile
 
-template <typename Real, int N>
-__global__ void __launch_bounds__(PassCfg<Real, N>::THREADS) fft_pass_kernel(const PassArgs a) {
-    using Cfg = PassCfg<Real, N>;
+// The whole pass for one tile of lines.  Threads tid >= THREADS (a CTA shared
+// by several line lengths, see the grouped serving kernel) take part in the
+// barriers only.
+template <typename Real, int N, int TC>
+__device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned char *smem_raw, const int tid) {
+    using Cfg = PassCfg<Real, N, TC>;
     using C = typename Cfg::C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
     C *tw = buf + Cfg::DATA;
-    int64_t *lbase = reinterpret_cast<int64_t *>(tw + N);  // input offset of each line of the tile
+    int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);  // input offset of each tile line
+    const bool active = tid < Cfg::THREADS;
 
-    const int tid = threadIdx.x;
     const C *in = reinterpret_cast<const C *>(a.in);
     C *out = reinterpret_cast<C *>(a.out);
     const C *gtw = reinterpret_cast<const C *>(a.tw);
 
     // tile coordinates
-    int64_t t = blockIdx.x;
     const int64_t gb = t % a.gblocks;
     t /= a.gblocks;
     const int64_t hb = t % a.hblocks;
@@ -316,44 +359,50 @@ __global__ void __launch_bounds__(PassCfg<Real, N>::THREADS) fft_pass_kernel(con
         out_base += c * a.rest_out[i];
     }
 
-    for (int q = tid; q < N; q += Cfg::THREADS) tw[q] = gtw[q];
-    if (tid < Cfg::LINES) {
-        const int bg = tid % a.Bg, bh = tid / a.Bg;
-        lbase[tid] = in_base + bg * a.in_sg + bh * a.in_sh;
+    if (active) {
+        for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
+        if constexpr (TC != 0) tc_build_bfrag<TC, Cfg::THREADS>(reinterpret_cast<uint32_t *>(tw + Cfg::TWN), tid);
+        if (tid < Cfg::LINES) {
+            const int bg = tid % a.Bg, bh = tid / a.Bg;
+            lbase[tid] = in_base + bg * a.in_sg + bh * a.in_sh;
+        }
     }
     __syncthreads();
 
     // FFT role: thread (line, t) with t fastest
     const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
     const int fbg = line % a.Bg, fbh = line / a.Bg;
-    const bool fok = line < a.Bg * a.Bh && g0 + fbg < a.Ng && h0 + fbh < a.Nh;
+    const bool fok = active && line < a.Bg * a.Bh && g0 + fbg < a.Ng && h0 + fbh < a.Nh;
 
     if constexpr (!Cfg::DIRECT) {  // stage the whole tile through shared memory
-        for (int e = tid; e < Cfg::LINES * N; e += Cfg::THREADS) {
-            const int l = e / N, i = e % N;
-            const int bg = l % a.Bg, bh = l / a.Bg;
-            if (l < a.Bg * a.Bh && g0 + bg < a.Ng && h0 + bh < a.Nh) {
-                C x = in[lbase[l] + i];
-                if (a.conj) x.y = -x.y;
-                buf[l * Cfg::PADN + pad16(i)] = x;
+        if (active) {
+            for (int e = tid; e < Cfg::LINES * N; e += Cfg::THREADS) {
+                const int l = e / N, i = e % N;
+                const int bg = l % a.Bg, bh = l / a.Bg;
+                if (l < a.Bg * a.Bh && g0 + bg < a.Ng && h0 + bh < a.Nh) {
+                    C x = in[lbase[l] + i];
+                    if (a.conj) x.y = -x.y;
+                    buf[l * Cfg::PADN + pad16(i)] = x;
+                }
             }
         }
         __syncthreads();
     }
     if constexpr (Cfg::plan.S == 0) {  // length-1 lines: the DFT is the identity
-        const C v = buf[line * Cfg::PADN];
+        C v = C{0, 0};
+        if (active) v = buf[line * Cfg::PADN];
         __syncthreads();
-        buf[line] = v;  // tile[k = 0][line]
+        if (active) buf[line] = v;  // tile[k = 0][line]
         __syncthreads();
     } else {
         const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
-        Stages<Real, N, 0, 1>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0);
+        Stages<Real, N, 0, 1, TC>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0, active);
     }
 
     // store role: thread owns line sl and writes k = k0, k0 + TL, ...
     const int sl = tid % Cfg::LINES, k0 = tid / Cfg::LINES;
     const int sbg = sl % a.Bg, sbh = sl / a.Bg;
-    const bool sok = sl < a.Bg * a.Bh && g0 + sbg < a.Ng && h0 + sbh < a.Nh;
+    const bool sok = active && sl < a.Bg * a.Bh && g0 + sbg < a.Ng && h0 + sbh < a.Nh;
     unsigned long long moved = 0, split = 0;
     if (sok) {
         const int64_t obase = out_base + sbh * a.out_sh + sbg;
@@ -383,6 +432,14 @@ __global__ void __launch_bounds__(PassCfg<Real, N>::THREADS) fft_pass_kernel(con
             if (split) atomicAdd(a.split, split);
         }
     }
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <typename Real, int N, int TC = 0>
+__global__ void __launch_bounds__(PassCfg<Real, N, TC>::THREADS) fft_pass_kernel(const PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pass_tile<Real, N, TC>(a, blockIdx.x, smem_raw, threadIdx.x);
 }
 
 }  // namespace mdfft

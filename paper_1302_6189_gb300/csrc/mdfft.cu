@@ -87,9 +87,17 @@ mdfft::OwnerMap owner_map(int M, const int64_t *N, int64_t P, const pl::Layout &
     return m;
 }
 
+// Kernel for a line length: the tensor-core dtypes use the tensor-core
+// variant when the length is a multiple of 16 (radix-16 stages exist) and the
+// FP32 SIMT kernel otherwise.
 bool lookup(mdfft_dtype dt, int64_t n, PassKernel *k) {
     if (dt == MDFFT_C64) return mdfft::find_pass_kernel_c64(n, k);
     if (dt == MDFFT_C128) return mdfft::find_pass_kernel_c128(n, k);
+    if (dt == MDFFT_C64_TC_FP16 || dt == MDFFT_C64_TC_BF16) {
+        const int tc = dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16;
+        if (mdfft::find_pass_kernel_tc(n, tc, k)) return true;
+        return mdfft::find_pass_kernel_c64(n, k);
+    }
     return false;
 }
 
@@ -165,13 +173,27 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     return MDFFT_OK;
 }
 
-__global__ void twiddle_kernel(void *dst, int64_t n, int dbl) {
+// Twiddle table of one pass (layout of tw_offset in fft_pass.cuh): entry
+// r * NS + k of stage s >= 1 is w_N^e, e = k r N / (NS R), w_N = exp(-2 pi i/N),
+// computed in FP64 with sincospi and rounded to the pass precision.
+__global__ void twiddle_kernel(void *dst, int64_t n, mdfft::RadixPlan plan, int dbl) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    double s, c;
-    sincospi(-2.0 * (double)q / (double)n, &s, &c);  // w_n^q = exp(-2 pi i q / n)
-    if (dbl) reinterpret_cast<double2 *>(dst)[q] = make_double2(c, s);
-    else reinterpret_cast<float2 *>(dst)[q] = make_float2((float)c, (float)s);
+    if (q >= mdfft::tw_entries(plan)) return;
+    int64_t off = 0, ns = plan.R[0];
+    for (int s = 1; s < plan.S; ++s) {
+        const int64_t R = plan.R[s];
+        if (q < off + ns * R) {
+            const int64_t r = (q - off) / ns, k = (q - off) % ns;
+            const int64_t e = (k * r * (n / (ns * R))) % n;
+            double sv, cv;
+            sincospi(-2.0 * (double)e / (double)n, &sv, &cv);
+            if (dbl) reinterpret_cast<double2 *>(dst)[q] = make_double2(cv, sv);
+            else reinterpret_cast<float2 *>(dst)[q] = make_float2((float)cv, (float)sv);
+            return;
+        }
+        off += ns * R;
+        ns *= R;
+    }
 }
 
 mdfft_status parse_order(int M, const int *order, std::vector<pl::Layout> &out) {
@@ -277,11 +299,8 @@ mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, 
     *out = nullptr;
     if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
     if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE)) return fail(MDFFT_E_ARG, "unknown flag");
-    if (dt != MDFFT_C64 && dt != MDFFT_C128) {
-        if (dt == MDFFT_C64_TC_FP16 || dt == MDFFT_C64_TC_BF16)
-            return fail(MDFFT_E_UNSUPPORTED, "tensor-core dtypes are not built");
+    if (dt != MDFFT_C64 && dt != MDFFT_C128 && dt != MDFFT_C64_TC_FP16 && dt != MDFFT_C64_TC_BF16)
         return fail(MDFFT_E_ARG, "unknown dtype");
-    }
     mdfft_plan_s *p = new (std::nothrow) mdfft_plan_s;
     if (!p) return fail(MDFFT_E_NOMEM, "host allocation");
     p->M = M, p->P = P, p->dt = dt, p->flags = flags;
@@ -337,7 +356,8 @@ mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, 
         size_t off = 0;
         for (int s = 0; s < M; ++s) {
             p->pass[s].tw_offset = off;
-            off += ((size_t)p->pass[s].n * p->elem + 255) / 256 * 256;
+            const size_t entries = std::max(1, mdfft::tw_entries(p->pass[s].k.plan));
+            off += (entries * p->elem + 255) / 256 * 256;
         }
         p->tw_bytes = off;
         cudaError_t e = cudaMalloc(&p->tw, off);
@@ -346,9 +366,10 @@ mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, 
             return cuda_fail(e, "cudaMalloc twiddles");
         }
         for (int s = 0; s < M; ++s) {
-            int64_t n = p->pass[s].n;
-            twiddle_kernel<<<(unsigned)((n + 255) / 256), 256>>>((char *)p->tw + p->pass[s].tw_offset, n,
-                                                                 dt == MDFFT_C128);
+            const int64_t n = p->pass[s].n;
+            const int entries = std::max(1, mdfft::tw_entries(p->pass[s].k.plan));
+            twiddle_kernel<<<(unsigned)((entries + 255) / 256), 256>>>((char *)p->tw + p->pass[s].tw_offset, n,
+                                                                       p->pass[s].k.plan, dt == MDFFT_C128);
         }
         const size_t bytes = (size_t)p->T * p->elem;
         if ((e = cudaMalloc(&p->ws, bytes)) != cudaSuccess) {
@@ -571,7 +592,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[MDFFT_NOALLOC_S
 
 namespace {
 
-constexpr size_t kNoallocTwiddleBytes = 256 * 1024;  // M tables of at most 1024 x 16 bytes
+constexpr size_t kNoallocTwiddleBytes = 256 * 1024;  // M <= 8 tables of at most 2048 x 16 bytes
+constexpr size_t kNoallocTwiddleStride = 2048;       // entries reserved per pass (tw_entries < 2 N <= 2048)
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
@@ -699,9 +721,9 @@ extern "C" mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     // twiddles of every pass, rewritten by every call in stream order
     for (int s = 0; s < M; ++s) {
-        const int64_t n = pass[s].n;
-        twiddle_kernel<<<(unsigned)((n + 255) / 256), 256, 0, cs>>>(scratch + (size_t)s * 1024 * elem, n,
-                                                                   dt == MDFFT_C128);
+        const int entries = std::max(1, mdfft::tw_entries(pass[s].k.plan));
+        twiddle_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, cs>>>(
+            scratch + (size_t)s * kNoallocTwiddleStride * elem, pass[s].n, pass[s].k.plan, dt == MDFFT_C128);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "twiddle launch");
@@ -718,7 +740,7 @@ extern "C" mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *
         PassArgs a = pass[s].args;
         a.in = src;
         a.out = dst[s];
-        a.tw = scratch + (size_t)s * 1024 * elem;
+        a.tw = scratch + (size_t)s * kNoallocTwiddleStride * elem;
         a.conj = dir == 1;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)T : 1.0;
         void *args[] = {&a};

@@ -5,7 +5,7 @@ namespace mdfft {
 
 template <int N> static PassKernel make_c64() {
     using Cfg = PassCfg<float, N>;
-    return PassKernel{(const void *)&fft_pass_kernel<float, N>, Cfg::THREADS, Cfg::LINES, Cfg::TL, Cfg::SMEM};
+    return PassKernel{(const void *)&fft_pass_kernel<float, N>, Cfg::THREADS, Cfg::LINES, Cfg::TL, Cfg::SMEM, Cfg::plan};
 }
 
 bool find_pass_kernel_c64(int64_t n, PassKernel *k) {

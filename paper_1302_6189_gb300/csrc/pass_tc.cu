@@ -1,0 +1,27 @@
+// pass_tc.cu -- instantiations of the fused pass kernel with tensor-core radix-16 stages
+// (complex64 data; split hi/lo FP16 or BF16 operands, FP32 accumulation).
+#include "passes.h"
+
+namespace mdfft {
+
+template <int N, int TC> static PassKernel make_tc() {
+    using Cfg = PassCfg<float, N, TC>;
+    return PassKernel{(const void *)&fft_pass_kernel<float, N, TC>, Cfg::THREADS, Cfg::LINES, Cfg::TL, Cfg::SMEM,
+                      Cfg::plan};
+}
+
+bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k) {
+    if (tc != kTcFp16 && tc != kTcBf16) return false;
+    switch (n) {
+#define MDFFT_CASE(N)                                                     \
+    case N:                                                               \
+        *k = tc == kTcFp16 ? make_tc<N, kTcFp16>() : make_tc<N, kTcBf16>(); \
+        return true;
+        MDFFT_TC_LENGTHS(MDFFT_CASE)
+#undef MDFFT_CASE
+        default:
+            return false;
+    }
+}
+
+}  // namespace mdfft

@@ -13,15 +13,22 @@
         X(80) X(96) X(120) X(128) X(160) X(192) X(240) X(256) X(320) X(384) X(480) X(512) X(640) X(768)    \
             X(960) X(1024)
 
+// Line lengths with a tensor-core variant (a multiple of 16 in the list above).
+#define MDFFT_TC_LENGTHS(X)                                                                                    \
+    X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(240) X(256) X(320) X(384) X(480) X(512) X(640) \
+        X(768) X(960) X(1024)
+
 namespace mdfft {
 
 struct PassKernel {
     const void *fn;  // __global__ fft_pass_kernel<Real, N>
     int threads, lines, tl;
     size_t smem;
+    RadixPlan plan;  // radix plan of the kernel; its twiddle table follows tw_offset()
 };
 
 bool find_pass_kernel_c64(int64_t n, PassKernel *k);
 bool find_pass_kernel_c128(int64_t n, PassKernel *k);
+bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k);  // tc: kTcFp16 or kTcBf16
 
 }  // namespace mdfft

@@ -1,0 +1,86 @@
+"""Tensor-core dtypes (radix-16 stages as FP16 or BF16 split hi/lo GEMMs with
+FP32 accumulation) against the FP64 oracle.
+
+Stated bounds (relative L2 over the result):
+  MDFFT_C64_TC_FP16: 1e-5.  hi + lo carries 22 bits of every operand and the
+    dropped lo*lo product is below 2^-22, so the stage error is that of FP32
+    arithmetic (~1e-7 per stage); 1e-5 is the ceiling.
+  MDFFT_C64_TC_BF16: 1e-4.  hi + lo carries 16 bits (BF16 has 8), so each
+    radix-16 stage adds ~2^-17 relative error; with up to two radix-16
+    stages per pass and three passes the RMS stays near 1e-5; 1e-4 is the
+    ceiling.
+Lines whose length is not a multiple of 16 run on the FP32 SIMT kernel.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1302_6189_gb300 as md
+import synth_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64_tc_fp16": 1e-5, "c64_tc_bf16": 1e-4}
+DEV = torch.device("cuda:0")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run(shape, P, order, dt, x, dir=-1, normalize=False):
+    with md.Plan(shape, P, order, dt) as plan:
+        xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).to(DEV)
+        y = plan.exec(xd, dir=dir, normalize=normalize)
+        torch.cuda.synchronize()
+        return y.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("dt", ["c64_tc_fp16", "c64_tc_bf16"])
+@pytest.mark.parametrize("shape", [(64, 48, 32), (16, 80, 24), (512, 16, 6), (32, 1024, 2), (240, 160, 12),
+                                   (96, 96, 96), (16, 16, 16, 16), (32, 48, 16, 8, 4)])
+def test_tc_matches_oracle(dt, shape):
+    x = si.gaussian_complex(shape, 1306)
+    ref = oracle.fftn(x, nthreads=8)
+    for order in (None, "worst"):
+        o = None
+        if order == "worst":
+            o, _ = md.mdfft_order_search(shape, 7, 1)
+        y = run(shape, 7, o, dt, x)
+        e = rel_l2(y, ref)
+        assert e <= TOL[dt], (shape, dt, e)
+    yi = run(shape, 7, None, dt, x, dir=+1)
+    assert rel_l2(yi, oracle.fftn(x, sign=+1, nthreads=8)) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c64_tc_fp16", "c64_tc_bf16"])
+def test_tc_round_trip_and_large_values(dt):
+    shape = (128, 64, 32)
+    x = si.gaussian_complex(shape, 77) * 3e4  # FP16 range needs the per-row scale
+    y = run(shape, 16, None, dt, x)
+    assert rel_l2(y, oracle.fftn(x, nthreads=8)) <= TOL[dt]
+    back = run(shape, 16, None, dt, y, dir=+1, normalize=True)
+    assert rel_l2(back, x) <= 2 * TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c64_tc_fp16", "c64_tc_bf16"])
+def test_tc_512cubed_sampled(dt):
+    shape = (512, 512, 512)
+    x = si.gaussian_complex(shape, si.SEEDS["precision512"], dtype=np.complex64)
+    with md.Plan(shape, 4096, None, dt) as plan:
+        y = plan.exec(torch.from_numpy(x).to(DEV))
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy()
+    x128 = x.astype(np.complex128)
+    rng = np.random.default_rng(9)
+    rms = np.sqrt(x.size * 2.0)
+    errs = []
+    for _ in range(4):
+        k = tuple(int(v) for v in rng.integers(0, 512, size=3))
+        errs.append(abs(complex(yh[k]) - oracle.dft_point(x128, k)))
+    assert max(errs) <= 10 * TOL[dt] * rms, errs
+    lhs = float(np.sum(np.abs(yh.astype(np.complex128)) ** 2))
+    rhs = float(x.size * np.sum(np.abs(x128) ** 2))
+    assert abs(lhs - rhs) <= 2 * TOL[dt] * rhs
