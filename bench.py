@@ -430,6 +430,7 @@ def extra_table(dev, x, P):
                    "nominal_tflops_fp64": round(flops / (ms * 1e-3) / 1e12, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms]}
     res["precision_512cubed"] = precision_study(dev)
+    res["serving"] = serving_study(dev)
     return res
 
 
@@ -486,6 +487,107 @@ def profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": f"256^3 {args.profile_dtype} forward", "order": plan.order_str(),
                           "passes": plan.describe()}))
+
+
+def serving_study(dev, n=2000, budget=40e9):
+    """2000 Poisson arrivals: 80 % 3-D requests with axes from {48..192}, 20 %
+    32^4, complex64 forward, 40 GB HBM admission budget.  The batched server
+    (one graph launch of one persistent kernel per step) against plain
+    per-request mdfft_exec launches of the same kernels, at arrival rates
+    0.5, 0.8 and 1.0 times the server's saturated throughput X.  Latency is
+    arrival (host clock) to completion (CUDA event), both from one zero."""
+    import numpy as np
+    import torch
+
+    import synth_inputs as si
+    from paper_1302_6189_gb300 import Plan, Server
+
+    shapes = si.serving_requests(n, si.SEEDS["serving"])
+    distinct = sorted(set(shapes))
+    gen = torch.Generator(device=dev)
+    inputs = {}
+    for k, shp in enumerate(distinct):
+        gen.manual_seed(si.SEEDS["serving"] * 1000 + k)
+        re = torch.rand(shp, generator=gen, device=dev) * 2 - 1
+        im = torch.rand(shp, generator=gen, device=dev) * 2 - 1
+        inputs[shp] = torch.complex(re, im)
+    outs = [torch.empty(shp, dtype=torch.complex64, device=dev) for shp in shapes]
+    bytes_per = [2 * len(shp) * int(np.prod(shp)) * 8 for shp in shapes]
+    stream = torch.cuda.current_stream(dev)
+
+    def run_server(srv, arrivals):
+        srv.reset_clock()
+        t0 = time.perf_counter()
+        ids, i = [], 0
+        while i < n:
+            now = time.perf_counter() - t0
+            while i < n and arrivals[i] <= now:
+                ids.append(srv.submit(inputs[shapes[i]], outs[i]))
+                i += 1
+            srv.step()
+        srv.drain()
+        done = []
+        for rid in ids:
+            ok, ms = srv.poll(rid)
+            done.append(ms / 1e3)
+            srv.release(rid)
+        return np.array(done)
+
+    plans = {shp: Plan(shp, 64, None, "c64") for shp in distinct}
+
+    def run_plain(arrivals):
+        torch.cuda.synchronize(dev)
+        t0ev = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        t0ev.record(stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        i = 0
+        while i < n:
+            now = time.perf_counter() - t0
+            while i < n and arrivals[i] <= now:
+                plans[shapes[i]].exec(inputs[shapes[i]], outs[i])
+                evs[i].record(stream)
+                i += 1
+        torch.cuda.synchronize(dev)
+        return np.array([t0ev.elapsed_time(e) / 1e3 for e in evs])
+
+    def summary(arrivals, done):
+        lat = (done - arrivals) * 1e3
+        span = float(done.max() - arrivals.min())
+        return {"fft_per_s": round(n / span, 1), "gbs": round(sum(bytes_per) / span / 1e9, 1),
+                "p50_ms": round(float(np.percentile(lat, 50)), 4), "p99_ms": round(float(np.percentile(lat, 99)), 4)}
+
+    zero = np.zeros(n)
+    with Server(int(budget), max_inflight=512, P=64) as srv:
+        for _ in range(2):  # plans, graphs and clocks warm
+            run_server(srv, zero)
+        # autotune the persistent grid: whole multiples of the SM count
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        best = None
+        for per_sm in (1, 2, 3, 4):
+            srv.set_grid(sms * per_sm)
+            t = float(run_server(srv, zero).max())
+            if best is None or t < best[0]:
+                best = (t, per_sm)
+        srv.set_grid(sms * best[1])
+        sat = run_server(srv, zero)
+        X = n / float(sat.max())
+        run_plain(zero)
+        plain_sat = run_plain(zero)
+        out = {"requests": n, "budget_gb": budget / 1e9, "grid_ctas_per_sm": best[1],
+               "saturated": {"batched": summary(zero, sat), "plain": summary(zero, plain_sat)}, "poisson": {}}
+        for frac in (0.5, 0.8, 1.0):
+            arrivals = si.poisson_arrivals(n, frac * X, si.SEEDS["serving"])
+            arrivals = arrivals - arrivals[0]
+            b = summary(arrivals, run_server(srv, arrivals))
+            p = summary(arrivals, run_plain(arrivals))
+            out["poisson"][f"{frac:.1f}X"] = {"rate_per_s": round(frac * X, 1), "batched": b, "plain": p}
+        out["server_stats"] = srv.stats()
+    for pl in plans.values():
+        pl.close()
+    out["results"] = "identical kernels and tiles in both arms (tests: bit-equal to mdfft_exec)"
+    return out
 
 
 def main():

@@ -209,6 +209,62 @@ int mdfft_supported_length(int64_t n, mdfft_dtype dt);
 mdfft_status mdfft_destroy(mdfft_plan_t plan);
 
 /*
+ * Serving: many M-D FFTs of different shapes, continuously batched.
+ * (Not in the paper; the engine runs the paper's passes of mdfft_exec.)
+ *
+ * A server owns a plan per shape (planner's best order for P virtual
+ * processes, complex64), a device arena for the workspaces of the requests
+ * in flight, and a CUDA graph per table slot.  mdfft_server_step() admits
+ * queued requests first come first served while the HBM budget (each request
+ * is charged input + output + workspace = 3 T 8 bytes) and the slot count
+ * allow, then launches -- as one graph launch of one persistent kernel -- the
+ * next pass of every request in flight, whatever its shape.  A request that
+ * arrives while others are on the GPU joins at the next step; it leaves after
+ * its last pass.  Requests advance one pass per step, so a step has no
+ * dependencies inside it and nothing waits on the device.  Line lengths
+ * 16, 24, 32, 48, 64, 96, 128, 160, 192, 256 run inside the persistent
+ * kernel; other supported lengths run as separate launches in the same step.
+ * Results are the same as mdfft_exec's for the same shape (same kernels and
+ * tiles).  All work goes to `stream`; the caller's buffers must stay valid
+ * until the request is done.  Errors: E_ARG, E_RANGE (request above the
+ * whole budget), E_UNSUPPORTED, E_NOMEM, E_CUDA.
+ */
+typedef struct mdfft_server_s *mdfft_server_t;
+
+typedef struct {
+    int64_t submitted, admitted, completed;
+    int64_t steps, graph_launches, kernel_launches;
+    int64_t inflight, queued;
+    size_t bytes_in_use, budget_bytes;
+    int grid_ctas; /* CTAs of the persistent kernel */
+} mdfft_server_stats;
+
+/* budget_bytes: HBM admission budget; max_inflight: 1..512 requests in
+ * flight; P: virtual processes of every request's plan (min(P, T)). */
+mdfft_status mdfft_server_create(mdfft_server_t *out, size_t budget_bytes, int max_inflight, int64_t P,
+                                 mdfft_stream_t stream);
+/* Queues one transform of dims N[0..M) from in_dev to out_dev (device
+ * complex64 arrays, not overlapping).  *request_id identifies it. */
+mdfft_status mdfft_server_submit(mdfft_server_t s, int M, const int64_t N[], const void *in_dev, void *out_dev,
+                                 int dir, int normalize, int64_t *request_id);
+/* One scheduling step (see above); *launched = 1 if work was launched. */
+mdfft_status mdfft_server_step(mdfft_server_t s, int *launched);
+/* *done = 1 once the request's result is in out_dev; *done_ms (may be NULL)
+ * is then its completion time on the server clock, in ms since the last
+ * mdfft_server_reset_clock (or creation), taken from CUDA events. */
+mdfft_status mdfft_server_poll(mdfft_server_t s, int64_t request_id, int *done, double *done_ms);
+/* Forget a finished request. */
+mdfft_status mdfft_server_release(mdfft_server_t s, int64_t request_id);
+/* Steps until every submitted request is done (blocks the host). */
+mdfft_status mdfft_server_drain(mdfft_server_t s);
+/* Sets the server clock's zero to now (records an event on the stream and waits for it). */
+mdfft_status mdfft_server_reset_clock(mdfft_server_t s);
+/* Re-captures the graphs with a persistent grid of `ctas` CTAs (autotuning). */
+mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas);
+mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out);
+mdfft_status mdfft_server_destroy(mdfft_server_t s);
+
+/*
  * mdfft_exec_noalloc -- the transform of mdfft_plan + mdfft_exec, for callers
  * that cannot let a library allocate GPU memory: applications whose device
  * memory is owned by their own allocator or memory pool, and loops where the

@@ -17,17 +17,19 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mdfft.h"
-#include "passes.h"
-#include "planner.h"
+#include "plan_internal.h"
 
 using mdfft::PassArgs;
 using mdfft::PassKernel;
+using mdfft::detail::Pass;
 namespace pl = mdfft::planner;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace mdfft {
+namespace detail {
 
 mdfft_status fail(mdfft_status st, const std::string &msg) {
     g_err = msg;
@@ -38,34 +40,11 @@ mdfft_status cuda_fail(cudaError_t e, const char *what) {
     return fail(MDFFT_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-struct Pass {
-    int f = 0, g = 0, h = -1;  // transformed axis, output's fastest axis, next tile axis
-    int64_t n = 0;             // line length N_f
-    PassKernel k{};
-    PassArgs args{};           // everything but in/out/tw/conj/scale/count pointers
-    int64_t ctas = 0;
-    size_t tw_offset = 0;      // byte offset of this pass's twiddle table
-};
+}  // namespace detail
+}  // namespace mdfft
 
-}  // namespace
-
-struct mdfft_plan_s {
-    int M = 0;
-    int64_t N[MDFFT_MAX_DIMS] = {0};
-    int64_t P = 0, T = 0;
-    mdfft_dtype dt = MDFFT_C64;
-    unsigned flags = 0;
-    size_t elem = 8;
-    std::vector<pl::Layout> order;
-    Pass pass[MDFFT_MAX_DIMS];
-    void *tw = nullptr, *ws = nullptr, *ws2 = nullptr;
-    size_t tw_bytes = 0;
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;  // MDFFT_TIMING_SLOTS x (M + 1) events, made on first enable
-    int64_t timed = 0;            // executions recorded since the last enable
-    bool comm_ready = false;
-    mdfft_comm comm{};
-};
+using mdfft::detail::cuda_fail;
+using mdfft::detail::fail;
 
 namespace {
 
@@ -228,6 +207,7 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
                        int64_t *counts) {
     if (!p) return fail(MDFFT_E_ARG, "null plan");
     if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan cannot execute");
+    if (p->external_ws) return fail(MDFFT_E_ARG, "plan has no workspace of its own");
     if (!in || !out) return fail(MDFFT_E_ARG, "null data pointer");
     if (dir != -1 && dir != 1) return fail(MDFFT_E_ARG, "dir must be -1 (forward) or +1 (inverse)");
     if (normalize != 0 && !(normalize == 1 && dir == 1))
@@ -294,6 +274,13 @@ int mdfft_supported_length(int64_t n, mdfft_dtype dt) {
 
 mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order, mdfft_dtype dt,
                         unsigned flags) {
+    return mdfft::detail::plan_create(out, M, N, P, order, dt, flags, true);
+}
+
+}  // extern "C"
+
+mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order,
+                                        mdfft_dtype dt, unsigned flags, bool with_workspace) {
     g_err.clear();
     if (!out || !N) return fail(MDFFT_E_ARG, "null argument");
     *out = nullptr;
@@ -372,11 +359,12 @@ mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, 
                                                                        p->pass[s].k.plan, dt == MDFFT_C128);
         }
         const size_t bytes = (size_t)p->T * p->elem;
-        if ((e = cudaMalloc(&p->ws, bytes)) != cudaSuccess) {
+        p->external_ws = !with_workspace;
+        if (with_workspace && (e = cudaMalloc(&p->ws, bytes)) != cudaSuccess) {
             release(p);
             return cuda_fail(e, "cudaMalloc workspace");
         }
-        if ((flags & MDFFT_PLAN_INPLACE) && (M % 2 == 1)) {
+        if (with_workspace && (flags & MDFFT_PLAN_INPLACE) && (M % 2 == 1)) {
             if ((e = cudaMalloc(&p->ws2, bytes)) != cudaSuccess) {
                 release(p);
                 return cuda_fail(e, "cudaMalloc second workspace");
@@ -400,6 +388,8 @@ mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, 
     *out = p;
     return MDFFT_OK;
 }
+
+extern "C" {
 
 mdfft_status mdfft_exec(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, mdfft_stream_t stream) {
     return exec_impl(p, in, out, dir, normalize, stream, nullptr);

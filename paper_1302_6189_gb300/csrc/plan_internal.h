@@ -1,0 +1,55 @@
+// plan_internal.h -- the plan object and helpers shared by the translation
+// units of libmdfft (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mdfft.h"
+#include "passes.h"
+#include "planner.h"
+
+namespace mdfft {
+namespace detail {
+
+struct Pass {
+    int f = 0, g = 0, h = -1;  // transformed axis, output's fastest axis, next tile axis
+    int64_t n = 0;             // line length N_f
+    PassKernel k{};
+    PassArgs args{};           // everything but in/out/tw/conj/scale/count pointers
+    int64_t ctas = 0;
+    size_t tw_offset = 0;      // byte offset of this pass's twiddle table
+};
+
+// Records the message for mdfft_last_error() on this thread; returns st.
+mdfft_status fail(mdfft_status st, const std::string &msg);
+mdfft_status cuda_fail(cudaError_t e, const char *what);
+
+// mdfft_plan without the plan's own workspace (its owner supplies one per
+// execution, as the server does).  exec on such a plan is refused.
+mdfft_status plan_create(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order, mdfft_dtype dt,
+                         unsigned flags, bool with_workspace);
+
+}  // namespace detail
+}  // namespace mdfft
+
+struct mdfft_plan_s {
+    int M = 0;
+    int64_t N[MDFFT_MAX_DIMS] = {0};
+    int64_t P = 0, T = 0;
+    mdfft_dtype dt = MDFFT_C64;
+    unsigned flags = 0;
+    size_t elem = 8;
+    std::vector<mdfft::planner::Layout> order;
+    mdfft::detail::Pass pass[MDFFT_MAX_DIMS];
+    void *tw = nullptr, *ws = nullptr, *ws2 = nullptr;
+    bool external_ws = false;     // made by plan_create(..., with_workspace = false)
+    size_t tw_bytes = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // MDFFT_TIMING_SLOTS x (M + 1) events, made on first enable
+    int64_t timed = 0;            // executions recorded since the last enable
+    bool comm_ready = false;
+    mdfft_comm comm{};
+};

@@ -1,0 +1,536 @@
+// serve.cu -- batched serving of M-D FFT requests of different shapes.
+//
+// Continuous batching at pass granularity.  Every step launches, in one
+// persistent kernel, the next pass (Fig. 4 step + transpose, as in
+// mdfft_exec) of every request in flight, whatever its shape; a request that
+// arrives while others are on the GPU joins at the next step, as soon as the
+// HBM budget and a slot allow, and leaves after its last pass.  One step is
+// one launch of a CUDA graph (copy of the step's work table from pinned host
+// memory, then the persistent kernel), captured once per table slot.  The
+// persistent kernel walks the tiles of all items with a grid stride; a CTA
+// finds the item of a tile by binary search over the items' first tiles and
+// runs the tile code of that item's line length.  There is no device-side
+// waiting: passes of one request are in consecutive steps, ordered by the
+// stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "plan_internal.h"
+
+using mdfft::PassArgs;
+using mdfft::detail::cuda_fail;
+using mdfft::detail::fail;
+
+namespace mdfft {
+namespace serve {
+
+constexpr int kMaxItems = 512;  // passes per step
+constexpr int kSlots = 4;       // tables (and graphs) in flight
+constexpr int kThreads = 512;   // CTA size of the persistent kernel
+
+// line lengths the persistent kernel carries (complex64); other lengths run
+// as separate launches of their own pass kernel within the same step
+#define MDFFT_SERVE_LENGTHS(X) X(0, 16) X(1, 24) X(2, 32) X(3, 48) X(4, 64) X(5, 96) X(6, 128) X(7, 160) X(8, 192) X(9, 256)
+constexpr int kKinds = 10;
+
+struct Item {
+    PassArgs args;
+    int64_t start;  // first tile of this item in the step's tile numbering
+    int kind;       // index into MDFFT_SERVE_LENGTHS
+    int pad;
+};
+
+struct Table {
+    int n;
+    int pad;
+    int64_t total;  // tiles in the step
+    Item items[kMaxItems];
+};
+
+template <int N> constexpr size_t smem_of() { return PassCfg<float, N, 0>::SMEM; }
+template <int N> constexpr int threads_of() { return PassCfg<float, N, 0>::THREADS; }
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+#define MDFFT_SMEM_MAX(i, N) cmax(smem_of<N>(),
+#define MDFFT_CLOSE(i, N) )
+constexpr size_t kSmem = MDFFT_SERVE_LENGTHS(MDFFT_SMEM_MAX) 0 MDFFT_SERVE_LENGTHS(MDFFT_CLOSE);
+#define MDFFT_THR_OK(i, N) static_assert(threads_of<N>() <= kThreads, "serve CTA too small");
+MDFFT_SERVE_LENGTHS(MDFFT_THR_OK)
+
+int kind_of(int64_t n) {
+    switch (n) {
+#define MDFFT_KIND(i, N) \
+    case N:              \
+        return i;
+        MDFFT_SERVE_LENGTHS(MDFFT_KIND)
+#undef MDFFT_KIND
+        default:
+            return -1;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) serve_kernel(const Table *tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PassArgs args;
+    const int n = tab->n;
+    const int64_t total = tab->total;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = n - 1;  // last item whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab->items[mid].start <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const Item &it = tab->items[lo];
+        {  // the item's arguments into shared memory
+            const int *src = reinterpret_cast<const int *>(&it.args);
+            int *dst = reinterpret_cast<int *>(&args);
+            for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        }
+        const int kind = it.kind;
+        const int64_t local = t - it.start;
+        __syncthreads();
+        switch (kind) {
+#define MDFFT_RUN(i, N)                                            \
+    case i:                                                        \
+        pass_tile<float, N, 0>(args, local, smem, threadIdx.x); \
+        break;
+            MDFFT_SERVE_LENGTHS(MDFFT_RUN)
+#undef MDFFT_RUN
+            default:
+                break;
+        }
+        __syncthreads();  // shared memory is reused by the next tile
+    }
+}
+
+// first-fit allocator over one device arena (offsets 256-byte aligned)
+class Arena {
+  public:
+    void reset(size_t bytes) {
+        free_.clear();
+        if (bytes) free_[0] = bytes;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+  private:
+    std::map<size_t, size_t> free_;
+};
+
+struct Request {
+    int64_t id = 0;
+    mdfft_plan_t plan = nullptr;
+    const void *in = nullptr;
+    void *out = nullptr;
+    int dir = -1, normalize = 0;
+    size_t bytes = 0;     // budget charge: input + output + workspace
+    size_t ws_off = 0;
+    bool has_ws = false;
+    int next_pass = 0;
+    bool admitted = false, finished = false;
+    double done_ms = -1.0;  // completion on the server clock
+    int slot = -1;          // slot of the step that ran the last pass
+};
+
+struct Slot {
+    Table *host = nullptr;  // pinned
+    Table *dev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<Request *> finishing;
+};
+
+}  // namespace serve
+}  // namespace mdfft
+
+using namespace mdfft::serve;
+
+struct mdfft_server_s {
+    size_t budget = 0, in_use = 0;
+    int max_inflight = 0;
+    int64_t P = 64;
+    cudaStream_t stream = nullptr, capture = nullptr;
+    int grid = 0;
+    void *arena_mem = nullptr;
+    size_t arena_bytes = 0;
+    Arena arena;
+    std::map<std::vector<int64_t>, mdfft_plan_t> plans;
+    std::deque<Request *> queue;
+    std::vector<Request *> inflight;
+    std::unordered_map<int64_t, Request *> requests;
+    int64_t next_id = 1;
+    Slot slots[kSlots];
+    int next_slot = 0;
+    cudaEvent_t t0 = nullptr;
+    mdfft_server_stats stats{};
+};
+
+namespace {
+
+mdfft_status capture_graphs(mdfft_server_t s) {
+    for (Slot &sl : s->slots) {
+        if (sl.exec) cudaGraphExecDestroy(sl.exec), sl.exec = nullptr;
+        if (sl.graph) cudaGraphDestroy(sl.graph), sl.graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        cudaMemcpyAsync(sl.dev, sl.host, sizeof(Table), cudaMemcpyHostToDevice, s->capture);
+        serve_kernel<<<s->grid, kThreads, kSmem, s->capture>>>(sl.dev);
+        e = cudaStreamEndCapture(s->capture, &sl.graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return MDFFT_OK;
+}
+
+// Requests of a slot whose step has completed: record completion, free memory.
+void resolve_slot(mdfft_server_t s, Slot &sl) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->t0, sl.done);
+    for (Request *r : sl.finishing) {
+        r->finished = true;
+        r->done_ms = ms;
+        if (r->has_ws) s->arena.release(r->ws_off, (size_t)r->plan->T * r->plan->elem);
+        r->has_ws = false;
+        s->in_use -= r->bytes;
+        s->stats.completed++;
+        s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), r));
+    }
+    sl.finishing.clear();
+    sl.busy = false;
+}
+
+void poll_slots(mdfft_server_t s) {
+    for (Slot &sl : s->slots)
+        if (sl.busy && cudaEventQuery(sl.done) == cudaSuccess) resolve_slot(s, sl);
+}
+
+mdfft_status get_plan(mdfft_server_t s, int M, const int64_t *N, mdfft_plan_t *out) {
+    std::vector<int64_t> key(N, N + M);
+    auto it = s->plans.find(key);
+    if (it != s->plans.end()) {
+        *out = it->second;
+        return MDFFT_OK;
+    }
+    int64_t T = 1;
+    for (int i = 0; i < M; ++i) T *= N[i];
+    mdfft_plan_t p = nullptr;
+    mdfft_status st = mdfft::detail::plan_create(&p, M, N, std::min<int64_t>(s->P, T), nullptr, MDFFT_C64, 0, false);
+    if (st != MDFFT_OK) return st;
+    s->plans[key] = p;
+    *out = p;
+    return MDFFT_OK;
+}
+
+// Pass s of request r as launch arguments (buffers as in mdfft_exec: the
+// last pass writes out, earlier ones alternate with the request's workspace).
+PassArgs pass_args(mdfft_server_t s, const Request *r, int pass) {
+    const mdfft_plan_s *p = r->plan;
+    const int M = p->M;
+    void *ws = (char *)s->arena_mem + r->ws_off;
+    const void *src = r->in;
+    void *dst = nullptr;
+    for (int q = 0; q <= pass; ++q) {
+        // destination of pass q going backwards from out
+        dst = ((M - 1 - q) % 2 == 0) ? r->out : ws;
+        if (q < pass) src = dst;
+    }
+    PassArgs a = p->pass[pass].args;
+    a.in = src;
+    a.out = dst;
+    a.tw = (const char *)p->tw + p->pass[pass].tw_offset;
+    a.conj = r->dir == 1;
+    a.scale = (pass == M - 1 && r->normalize) ? 1.0 / (double)p->T : 1.0;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdfft_status mdfft_server_create(mdfft_server_t *out, size_t budget_bytes, int max_inflight, int64_t P,
+                                 mdfft_stream_t stream) {
+    if (!out) return fail(MDFFT_E_ARG, "null argument");
+    *out = nullptr;
+    if (budget_bytes < 4096 || max_inflight < 1 || max_inflight > kMaxItems || P < 1)
+        return fail(MDFFT_E_ARG, "budget >= 4096 bytes, 1 <= max_inflight <= 512, P >= 1");
+    mdfft_server_s *s = new (std::nothrow) mdfft_server_s;
+    if (!s) return fail(MDFFT_E_NOMEM, "host allocation");
+    s->budget = budget_bytes;
+    s->max_inflight = max_inflight;
+    s->P = P;
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+    s->stats.budget_bytes = budget_bytes;
+    auto bail = [&](mdfft_status st) {
+        mdfft_server_destroy(s);
+        return st;
+    };
+    cudaError_t e;
+    // workspaces: one T-element array per request in flight; each request is
+    // charged input + output + workspace, so workspaces use at most a third
+    s->arena_bytes = (budget_bytes / 3 + 255) / 256 * 256;
+    if ((e = cudaMalloc(&s->arena_mem, s->arena_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc arena"));
+    s->arena.reset(s->arena_bytes);
+    if ((e = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaStreamCreate"));
+    if ((e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "cudaFuncSetAttribute"));
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kThreads, kSmem);
+    s->grid = std::max(1, sms * std::max(1, per_sm));
+    for (Slot &sl : s->slots) {
+        if ((e = cudaHostAlloc((void **)&sl.host, sizeof(Table), cudaHostAllocDefault)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaHostAlloc table"));
+        std::memset(sl.host, 0, sizeof(Table));
+        if ((e = cudaMalloc((void **)&sl.dev, sizeof(Table))) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMalloc table"));
+        if ((e = cudaEventCreate(&sl.done)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
+    mdfft_status st = capture_graphs(s);
+    if (st != MDFFT_OK) return bail(st);
+    s->stats.grid_ctas = s->grid;
+    if ((e = cudaEventCreate(&s->t0)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    cudaEventRecord(s->t0, s->stream);
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
+    *out = s;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_submit(mdfft_server_t s, int M, const int64_t N[], const void *in_dev, void *out_dev,
+                                 int dir, int normalize, int64_t *request_id) {
+    if (!s || !N || !in_dev || !out_dev || !request_id) return fail(MDFFT_E_ARG, "null argument");
+    if (dir != -1 && dir != 1) return fail(MDFFT_E_ARG, "dir must be -1 or +1");
+    if (normalize != 0 && !(normalize == 1 && dir == 1)) return fail(MDFFT_E_ARG, "normalize only on the inverse");
+    if ((uintptr_t)in_dev % 8 || (uintptr_t)out_dev % 8) return fail(MDFFT_E_ARG, "misaligned data pointer");
+    mdfft_plan_t p = nullptr;
+    mdfft_status st = get_plan(s, M, N, &p);
+    if (st != MDFFT_OK) return st;
+    const size_t bytes = (size_t)p->T * p->elem;
+    const uintptr_t a = (uintptr_t)in_dev, b = (uintptr_t)out_dev;
+    if (a < b + bytes && b < a + bytes) return fail(MDFFT_E_ARG, "in and out overlap");
+    if (3 * bytes > s->budget) return fail(MDFFT_E_RANGE, "request larger than the whole HBM budget");
+    Request *r = new (std::nothrow) Request;
+    if (!r) return fail(MDFFT_E_NOMEM, "host allocation");
+    r->id = s->next_id++;
+    r->plan = p;
+    r->in = in_dev;
+    r->out = out_dev;
+    r->dir = dir;
+    r->normalize = normalize;
+    r->bytes = 3 * bytes;
+    s->requests[r->id] = r;
+    s->queue.push_back(r);
+    s->stats.submitted++;
+    *request_id = r->id;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
+    if (!s) return fail(MDFFT_E_ARG, "null server");
+    if (launched) *launched = 0;
+    poll_slots(s);
+    // admission: first come first served, within the budget, the slots and the arena
+    while (!s->queue.empty() && (int)s->inflight.size() < s->max_inflight) {
+        Request *r = s->queue.front();
+        if (s->in_use + r->bytes > s->budget) break;
+        size_t off = 0;
+        if (!s->arena.alloc((size_t)r->plan->T * r->plan->elem, &off)) break;
+        r->ws_off = off;
+        r->has_ws = true;
+        r->admitted = true;
+        s->in_use += r->bytes;
+        s->inflight.push_back(r);
+        s->queue.pop_front();
+        s->stats.admitted++;
+    }
+    std::vector<Request *> todo;
+    for (Request *r : s->inflight)
+        if (r->next_pass < r->plan->M) todo.push_back(r);
+    if (todo.empty()) return MDFFT_OK;
+    Slot &sl = s->slots[s->next_slot];
+    if (sl.busy) {  // its table may still be in use: wait for that step
+        cudaError_t e = cudaEventSynchronize(sl.done);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        resolve_slot(s, sl);
+    }
+    Table *tab = sl.host;
+    int n = 0;
+    int64_t total = 0;
+    std::vector<std::pair<Request *, PassArgs>> separate;  // lengths the persistent kernel does not carry
+    for (Request *r : todo) {
+        if (n >= kMaxItems) break;
+        const int pass = r->next_pass;
+        const PassArgs a = pass_args(s, r, pass);
+        const int kind = kind_of(r->plan->pass[pass].n);
+        if (kind < 0) {
+            separate.push_back({r, a});
+        } else {
+            Item &it = tab->items[n++];
+            it.args = a;
+            it.start = total;
+            it.kind = kind;
+            total += r->plan->pass[pass].ctas;
+        }
+        r->next_pass++;
+        if (r->next_pass == r->plan->M) {
+            r->slot = s->next_slot;
+            sl.finishing.push_back(r);
+        }
+    }
+    tab->n = n;
+    tab->total = total;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaGraphLaunch(sl.exec, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        s->stats.graph_launches++;
+        s->stats.kernel_launches++;
+    }
+    for (auto &pr : separate) {
+        const mdfft::detail::Pass &ps = pr.first->plan->pass[pr.first->next_pass - 1];
+        PassArgs a = pr.second;
+        void *args[] = {&a};
+        e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)ps.ctas), dim3(ps.k.threads), args, ps.k.smem, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+        s->stats.kernel_launches++;
+    }
+    e = cudaEventRecord(sl.done, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    sl.busy = true;
+    s->next_slot = (s->next_slot + 1) % kSlots;
+    s->stats.steps++;
+    if (launched) *launched = 1;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_poll(mdfft_server_t s, int64_t request_id, int *done, double *done_ms) {
+    if (!s || !done) return fail(MDFFT_E_ARG, "null argument");
+    auto it = s->requests.find(request_id);
+    if (it == s->requests.end()) return fail(MDFFT_E_ARG, "unknown request id");
+    Request *r = it->second;
+    if (!r->finished && r->slot >= 0) {
+        Slot &sl = s->slots[r->slot];
+        if (sl.busy && cudaEventQuery(sl.done) == cudaSuccess) resolve_slot(s, sl);
+    }
+    *done = r->finished ? 1 : 0;
+    if (done_ms) *done_ms = r->finished ? r->done_ms : -1.0;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_release(mdfft_server_t s, int64_t request_id) {
+    if (!s) return fail(MDFFT_E_ARG, "null server");
+    auto it = s->requests.find(request_id);
+    if (it == s->requests.end()) return fail(MDFFT_E_ARG, "unknown request id");
+    if (!it->second->finished) return fail(MDFFT_E_ARG, "request not finished");
+    delete it->second;
+    s->requests.erase(it);
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_drain(mdfft_server_t s) {
+    if (!s) return fail(MDFFT_E_ARG, "null server");
+    while (!s->queue.empty() || !s->inflight.empty()) {
+        int launched = 0;
+        mdfft_status st = mdfft_server_step(s, &launched);
+        if (st != MDFFT_OK) return st;
+        if (!launched) {  // nothing left to launch: wait for the steps in flight
+            for (Slot &sl : s->slots)
+                if (sl.busy) {
+                    cudaError_t e = cudaEventSynchronize(sl.done);
+                    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+                    resolve_slot(s, sl);
+                }
+        }
+    }
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_reset_clock(mdfft_server_t s) {
+    if (!s) return fail(MDFFT_E_ARG, "null server");
+    cudaEventRecord(s->t0, s->stream);
+    cudaError_t e = cudaEventSynchronize(s->t0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas) {
+    if (!s || ctas < 1) return fail(MDFFT_E_ARG, "bad argument");
+    for (Slot &sl : s->slots)
+        if (sl.busy) {
+            cudaError_t e = cudaEventSynchronize(sl.done);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+            resolve_slot(s, sl);
+        }
+    s->grid = ctas;
+    s->stats.grid_ctas = ctas;
+    return capture_graphs(s);
+}
+
+mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out) {
+    if (!s || !out) return fail(MDFFT_E_ARG, "null argument");
+    s->stats.inflight = (int64_t)s->inflight.size();
+    s->stats.queued = (int64_t)s->queue.size();
+    s->stats.bytes_in_use = s->in_use;
+    *out = s->stats;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_destroy(mdfft_server_t s) {
+    if (!s) return MDFFT_OK;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (Slot &sl : s->slots) {
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.graph) cudaGraphDestroy(sl.graph);
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (s->t0) cudaEventDestroy(s->t0);
+    if (s->capture) cudaStreamDestroy(s->capture);
+    if (s->arena_mem) cudaFree(s->arena_mem);
+    for (auto &kv : s->plans) mdfft_destroy(kv.second);
+    for (auto &kv : s->requests) delete kv.second;
+    delete s;
+    return MDFFT_OK;
+}
+
+}  // extern "C"

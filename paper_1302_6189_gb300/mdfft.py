@@ -44,6 +44,12 @@ class MdfftPassInfo(ctypes.Structure):
                 ("smem_bytes", c_int), ("ctas", i64), ("fft_axis", c_int), ("store_axis", c_int)]
 
 
+class MdfftServerStats(ctypes.Structure):
+    _fields_ = [("submitted", i64), ("admitted", i64), ("completed", i64), ("steps", i64),
+                ("graph_launches", i64), ("kernel_launches", i64), ("inflight", i64), ("queued", i64),
+                ("bytes_in_use", c_size_t), ("budget_bytes", c_size_t), ("grid_ctas", c_int)]
+
+
 SIGNATURES = {
     "mdfft_plan": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint]),
     "mdfft_exec": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -62,6 +68,16 @@ SIGNATURES = {
     "mdfft_destroy": (c_int, [c_void_p]),
     "mdfft_exec_noalloc": (c_int, [c_int, P_(i64), P_(c_int), c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_last_error": (ctypes.c_char_p, []),
+    "mdfft_server_create": (c_int, [P_(c_void_p), c_size_t, c_int, i64, c_void_p]),
+    "mdfft_server_submit": (c_int, [c_void_p, c_int, P_(i64), c_void_p, c_void_p, c_int, c_int, P_(i64)]),
+    "mdfft_server_step": (c_int, [c_void_p, P_(c_int)]),
+    "mdfft_server_poll": (c_int, [c_void_p, i64, P_(c_int), P_(ctypes.c_double)]),
+    "mdfft_server_release": (c_int, [c_void_p, i64]),
+    "mdfft_server_drain": (c_int, [c_void_p]),
+    "mdfft_server_reset_clock": (c_int, [c_void_p]),
+    "mdfft_server_set_grid": (c_int, [c_void_p, c_int]),
+    "mdfft_server_get_stats": (c_int, [c_void_p, P_(MdfftServerStats)]),
+    "mdfft_server_destroy": (c_int, [c_void_p]),
 }
 
 
@@ -220,6 +236,60 @@ def mdfft_exec_noalloc(N, order, dtype, in_ptr, out_ptr, dir=-1, normalize=0, st
                                    int(normalize), c_void_p(stream)), "mdfft_exec_noalloc")
 
 
+def mdfft_server_create(budget_bytes, max_inflight, P=64, stream=0):
+    h = c_void_p()
+    _check(_lib.mdfft_server_create(ctypes.byref(h), int(budget_bytes), int(max_inflight), int(P),
+                                    c_void_p(stream)), "mdfft_server_create")
+    return h
+
+
+def mdfft_server_submit(server, N, in_ptr, out_ptr, dir=-1, normalize=0):
+    dims, M = _dims(N)
+    rid = i64()
+    _check(_lib.mdfft_server_submit(server, M, dims, c_void_p(in_ptr), c_void_p(out_ptr), int(dir), int(normalize),
+                                    ctypes.byref(rid)), "mdfft_server_submit")
+    return rid.value
+
+
+def mdfft_server_step(server):
+    launched = c_int()
+    _check(_lib.mdfft_server_step(server, ctypes.byref(launched)), "mdfft_server_step")
+    return bool(launched.value)
+
+
+def mdfft_server_poll(server, request_id):
+    done, ms = c_int(), ctypes.c_double()
+    _check(_lib.mdfft_server_poll(server, int(request_id), ctypes.byref(done), ctypes.byref(ms)),
+           "mdfft_server_poll")
+    return bool(done.value), ms.value
+
+
+def mdfft_server_release(server, request_id):
+    _check(_lib.mdfft_server_release(server, int(request_id)), "mdfft_server_release")
+
+
+def mdfft_server_drain(server):
+    _check(_lib.mdfft_server_drain(server), "mdfft_server_drain")
+
+
+def mdfft_server_reset_clock(server):
+    _check(_lib.mdfft_server_reset_clock(server), "mdfft_server_reset_clock")
+
+
+def mdfft_server_set_grid(server, ctas):
+    _check(_lib.mdfft_server_set_grid(server, int(ctas)), "mdfft_server_set_grid")
+
+
+def mdfft_server_get_stats(server):
+    st = MdfftServerStats()
+    _check(_lib.mdfft_server_get_stats(server, ctypes.byref(st)), "mdfft_server_get_stats")
+    return {f: getattr(st, f) for f, _ in MdfftServerStats._fields_}
+
+
+def mdfft_server_destroy(server):
+    _check(_lib.mdfft_server_destroy(server), "mdfft_server_destroy")
+
+
 def mdfft_last_error():
     return _lib.mdfft_last_error().decode(errors="replace")
 
@@ -312,6 +382,63 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None) is not None:
             mdfft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server on torch CUDA tensors (complex64)."""
+
+    def __init__(self, budget_bytes, max_inflight=256, P=64, stream=None):
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        self.stream = s
+        self.handle = mdfft_server_create(budget_bytes, max_inflight, P, s.cuda_stream)
+
+    def submit(self, x, out, dir=-1, normalize=False):
+        import torch
+        for t in (x, out):
+            if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+                raise ValueError("server requests take contiguous CUDA complex64 tensors")
+        if tuple(x.shape) != tuple(out.shape):
+            raise ValueError("input and output shapes differ")
+        return mdfft_server_submit(self.handle, tuple(x.shape), x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)))
+
+    def step(self):
+        return mdfft_server_step(self.handle)
+
+    def poll(self, rid):
+        return mdfft_server_poll(self.handle, rid)
+
+    def release(self, rid):
+        mdfft_server_release(self.handle, rid)
+
+    def drain(self):
+        mdfft_server_drain(self.handle)
+
+    def reset_clock(self):
+        mdfft_server_reset_clock(self.handle)
+
+    def set_grid(self, ctas):
+        mdfft_server_set_grid(self.handle, ctas)
+
+    def stats(self):
+        return mdfft_server_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            mdfft_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

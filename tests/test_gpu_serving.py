@@ -1,0 +1,116 @@
+"""The continuous-batching server: every result is the same alone (mdfft_exec
+of the same shape) and in a mix of shapes, requests join while others are in
+flight, and the HBM budget bounds what is admitted."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1302_6189_gb300 as md
+import synth_inputs as si
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def mixed_shapes(n, seed):
+    rng = np.random.default_rng(seed)
+    axes3 = [16, 24, 32, 48, 64]
+    out = []
+    for _ in range(n):
+        u = rng.uniform()
+        if u < 0.15:
+            out.append((16, 16, 16, 16))
+        elif u < 0.25:
+            out.append(tuple(int(v) for v in rng.choice([20, 40, 30, 16], size=3)))  # separate launches
+        else:
+            out.append(tuple(int(v) for v in rng.choice(axes3, size=3)))
+    return out
+
+
+def alone(shape, x, dir, normalize):
+    T = int(np.prod(shape))
+    with md.Plan(shape, min(64, T), None, "c64") as plan:
+        y = plan.exec(x, dir=dir, normalize=normalize)
+        torch.cuda.synchronize()
+    return y
+
+
+def test_mix_equals_alone_and_oracle():
+    shapes = mixed_shapes(48, 5)
+    rng = np.random.default_rng(6)
+    xs = [torch.from_numpy(si.uniform_complex(s, 500 + i, np.complex64)).to(DEV) for i, s in enumerate(shapes)]
+    outs = [torch.empty_like(x) for x in xs]
+    dirs = [int(rng.choice([-1, 1])) for _ in shapes]
+    with md.Server(budget_bytes=1 << 30, max_inflight=16, P=64) as srv:
+        ids = []
+        i = 0
+        while i < len(shapes):  # arrivals interleaved with steps: requests join mid-flight
+            for _ in range(int(rng.integers(1, 4))):
+                if i < len(shapes):
+                    ids.append(srv.submit(xs[i], outs[i], dir=dirs[i], normalize=dirs[i] == 1))
+                    i += 1
+            srv.step()
+        srv.drain()
+        st = srv.stats()
+        assert st["completed"] == len(shapes) and st["inflight"] == 0 and st["bytes_in_use"] == 0
+        assert st["graph_launches"] >= 1
+        for rid in ids:
+            done, ms = srv.poll(rid)
+            assert done and ms >= 0
+            srv.release(rid)
+    torch.cuda.synchronize()
+    for s, x, y, d in zip(shapes, xs, outs, dirs):
+        assert torch.equal(y, alone(s, x, d, d == 1)), s  # same kernels and tiles: identical bits
+    for k in range(0, len(shapes), 7):  # and against the oracle
+        ref = oracle.fftn(xs[k].cpu().numpy().astype(np.complex128), sign=dirs[k])
+        if dirs[k] == 1:
+            ref = ref / ref.size
+        y = outs[k].cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_budget_limits_admission():
+    shape = (64, 64, 64)
+    bytes_req = 3 * 64 ** 3 * 8
+    xs = [torch.from_numpy(si.uniform_complex(shape, 600 + i, np.complex64)).to(DEV) for i in range(6)]
+    outs = [torch.empty_like(x) for x in xs]
+    with md.Server(budget_bytes=2 * bytes_req + 4096, max_inflight=8) as srv:
+        for x, y in zip(xs, outs):
+            srv.submit(x, y)
+        peak = 0
+        for _ in range(200000):
+            srv.step()
+            st = srv.stats()
+            assert st["bytes_in_use"] <= st["budget_bytes"]
+            peak = max(peak, st["inflight"])
+            if st["completed"] == len(xs):
+                break
+        srv.drain()
+        assert peak <= 2
+    for x, y in zip(xs, outs):
+        assert torch.equal(y, alone(shape, x, -1, False))
+
+
+def test_single_cta_grid_and_errors():
+    shape = (32, 48, 16)
+    x = torch.from_numpy(si.uniform_complex(shape, 700, np.complex64)).to(DEV)
+    y = torch.empty_like(x)
+    with md.Server(budget_bytes=1 << 26, max_inflight=4) as srv:
+        srv.set_grid(1)  # one CTA walks every tile
+        srv.submit(x, y)
+        srv.drain()
+        assert srv.stats()["grid_ctas"] == 1
+        with pytest.raises(md.MdfftError) as e:
+            big = torch.empty((256, 256, 256), dtype=torch.complex64, device=DEV)
+            srv.submit(big, big)  # overlapping in/out
+        assert e.value.status == -1
+        with pytest.raises(md.MdfftError) as e:
+            a = torch.empty((256, 256, 256), dtype=torch.complex64, device=DEV)
+            b = torch.empty_like(a)
+            srv.submit(a, b)  # 3 x 128 MiB > 64 MiB budget
+        assert e.value.status == -3
+        with pytest.raises(md.MdfftError):
+            srv.poll(12345)
+    assert torch.equal(y, alone(shape, x, -1, False))
