@@ -57,6 +57,8 @@ def parse_args():
                     help="one warm-up and one profiled forward transform of one 256^3 complex64 volume "
                          "(3 + 3 pass launches), for ncu captures")
     ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
+    ap.add_argument("--serving-only", type=int, default=0, metavar="REQUESTS",
+                    help="run only the serving study with this many requests and print it")
     return ap.parse_args()
 
 
@@ -275,6 +277,8 @@ def run_ours(args):
     ys = [torch.empty_like(xs[0]) for _ in range(B)]
     zs = [torch.empty_like(xs[0]) for _ in range(B)]
     stream = torch.cuda.current_stream(dev)
+    tune_before, tune_after = plan.autotune(xs[0], ys[0], reps=20)
+    tuned = [{k: d[k] for k in ("threads", "tile_g", "tile_h", "ctas")} for d in plan.describe()]
 
     def step():
         for i in range(B):
@@ -359,7 +363,9 @@ def run_ours(args):
                    "P": P, "order": format_order(order, 3), "regimes": comm["regime"],
                    "comm_points_total": comm["total"], "l2": "inputs larger than L2 (8 x 128 MiB per step)",
                    "parallelism": f"replicas x{world}", "input": "U[-1,1) re/im, seeds 1303..1310",
-                   "roundtrip_rel_l2": err},
+                   "roundtrip_rel_l2": err, "autotune_ms_per_pass": {"default": [round(v, 5) for v in tune_before],
+                                                                      "chosen": [round(v, 5) for v in tune_after]},
+                   "passes": tuned},
         "roofline": {"kernel": "fft_pass_kernel<float,256>", "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
@@ -524,7 +530,7 @@ def serving_study(dev, n=2000, budget=40e9):
             while i < n and arrivals[i] <= now:
                 ids.append(srv.submit(inputs[shapes[i]], outs[i]))
                 i += 1
-            srv.step()
+            srv.run(4)  # up to one step per pass of a 4-D request
         srv.drain()
         done = []
         for rid in ids:
@@ -562,20 +568,24 @@ def serving_study(dev, n=2000, budget=40e9):
     with Server(int(budget), max_inflight=512, P=64) as srv:
         for _ in range(2):  # plans, graphs and clocks warm
             run_server(srv, zero)
-        # autotune the persistent grid: whole multiples of the SM count
+        # autotune the persistent grid (whole multiples of the SM count) and the
+        # number of steps in flight, on the saturated load
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         best = None
-        for per_sm in (1, 2, 3, 4):
-            srv.set_grid(sms * per_sm)
-            t = float(run_server(srv, zero).max())
-            if best is None or t < best[0]:
-                best = (t, per_sm)
+        for per_sm in (2, 4):
+            for depth in (1, 2, 4):
+                srv.set_grid(sms * per_sm)
+                srv.set_depth(depth)
+                t = float(run_server(srv, zero).max())
+                if best is None or t < best[0]:
+                    best = (t, per_sm, depth)
         srv.set_grid(sms * best[1])
+        srv.set_depth(best[2])
         sat = run_server(srv, zero)
         X = n / float(sat.max())
         run_plain(zero)
         plain_sat = run_plain(zero)
-        out = {"requests": n, "budget_gb": budget / 1e9, "grid_ctas_per_sm": best[1],
+        out = {"requests": n, "budget_gb": budget / 1e9, "grid_ctas_per_sm": best[1], "depth": best[2],
                "saturated": {"batched": summary(zero, sat), "plain": summary(zero, plain_sat)}, "poisson": {}}
         for frac in (0.5, 0.8, 1.0):
             arrivals = si.poisson_arrivals(n, frac * X, si.SEEDS["serving"])
@@ -594,6 +604,11 @@ def main():
     args = parse_args()
     if args.profile_case:
         profile_case(args)
+        return
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": serving_study(torch.device("cuda", 0), n=args.serving_only)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -197,6 +197,20 @@ typedef struct {
 } mdfft_pass_info;
 mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out);
 
+/*
+ * mdfft_plan_autotune -- for every pass, times the kernel variants built for
+ * its line length (the default launch shape and, for complex64 lengths 32,
+ * 48, 64, 96, 128, 160, 192, 256, 512, fixed 256- and 512-thread CTAs) with
+ * several tile shapes (lines along the output's fastest axis x lines along
+ * the next axis), `reps` launches each, and keeps the fastest.  Tiling never
+ * changes results.  in_dev (T elements, only read) and out_dev (T elements,
+ * overwritten with scratch) are the caller's; the call synchronises `stream`.
+ * ms_before / ms_after (M entries each, may be NULL) receive the mean pass
+ * times of the default and of the chosen configuration.
+ */
+mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *out_dev, int reps, mdfft_stream_t stream,
+                                 float *ms_before, float *ms_after);
+
 /* Device workspace the plan owns, in bytes (0 for host-only plans). */
 mdfft_status mdfft_workspace_size(mdfft_plan_t plan, size_t *bytes);
 
@@ -249,6 +263,10 @@ mdfft_status mdfft_server_submit(mdfft_server_t s, int M, const int64_t N[], con
                                  int dir, int normalize, int64_t *request_id);
 /* One scheduling step (see above); *launched = 1 if work was launched. */
 mdfft_status mdfft_server_step(mdfft_server_t s, int *launched);
+/* Up to max_steps steps in a row, stopping at the first that launches
+ * nothing; *steps (may be NULL) receives how many launched.  Requests
+ * admitted by the first step can run all their passes within one call. */
+mdfft_status mdfft_server_run(mdfft_server_t s, int max_steps, int *steps);
 /* *done = 1 once the request's result is in out_dev; *done_ms (may be NULL)
  * is then its completion time on the server clock, in ms since the last
  * mdfft_server_reset_clock (or creation), taken from CUDA events. */
@@ -261,6 +279,10 @@ mdfft_status mdfft_server_drain(mdfft_server_t s);
 mdfft_status mdfft_server_reset_clock(mdfft_server_t s);
 /* Re-captures the graphs with a persistent grid of `ctas` CTAs (autotuning). */
 mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas);
+/* Steps in flight on the GPU at most (1..8, default 2): a step is launched
+ * only while fewer are outstanding, so requests arriving meanwhile share the
+ * next step instead of each adding nearly empty ones. */
+mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth);
 mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out);
 mdfft_status mdfft_server_destroy(mdfft_server_t s);
 

@@ -104,12 +104,23 @@ __host__ __device__ constexpr RadixPlan radix_plan_tc(int n);
 
 // Launch configuration of the pass kernel for line length N.  TC != 0 selects
 // the tensor-core variant (complex64 only): radix-16 stages run as GEMMs.
-template <typename Real, int N, int TC = 0> struct PassCfg {
+// THR != 0 fixes the CTA at THR threads for every length (the persistent
+// serving kernel): a power-of-two number of threads per line and THR / that
+// many lines per tile (stage loops skip butterflies a thread does not own).
+__host__ __device__ constexpr int pow2ceil(int x) {
+    int p = 1;
+    while (p < x) p *= 2;
+    return p;
+}
+
+template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     using C = typename Cx<Real>::T;
     static_assert(TC == 0 || sizeof(Real) == 4, "tensor-core stages are complex64 only");
     static constexpr RadixPlan plan = TC ? radix_plan_tc(N) : radix_plan(N);
     static_assert(plan.S >= 0, "unsupported line length");  // S = 0: N = 1, a pure redistribution
-    static constexpr int TL = N / plan.maxR;  // threads per line
+    static constexpr int TL0 = N / plan.maxR;  // one butterfly per thread in the widest stage
+    static constexpr int kMinLines = 128 / (int)sizeof(C);
+    static constexpr int TL = THR ? (pow2ceil(TL0) < THR / kMinLines ? pow2ceil(TL0) : THR / kMinLines) : TL0;
     static constexpr int kTileElems = sizeof(Real) == 4 ? 4096 : 2048;
     // lines per tile: a power of two near kTileElems / N, at least enough for
     // 128-byte store runs (16 complex64 / 8 complex128), and a whole number
@@ -117,7 +128,8 @@ template <typename Real, int N, int TC = 0> struct PassCfg {
     // (tensor-core CTAs stay at <= 512 threads: their stages need ~100 registers)
     static constexpr int kMaxThreads = TC ? 512 : 1024;
     static constexpr int lines_for() {
-        int l = 128 / (int)sizeof(C);
+        if (THR) return THR / TL;
+        int l = kMinLines;
         while (l > 1 && TL * l > kMaxThreads) l /= 2;
         while (l < 256 && 2 * l * N <= kTileElems && 2 * TL * l <= kMaxThreads) l *= 2;
         while ((TL * l) % 32 != 0 && 2 * TL * l <= kMaxThreads) l *= 2;
@@ -257,8 +269,8 @@ __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
 // One Stockham stage with radix R after NS points already combined.
 // Butterfly j (< N/R) reads x[j + r N/R], applies w_{NS R}^{(j mod NS) r},
 // does DFT_R and writes y[(j / NS) NS R + j mod NS + r NS].
-template <typename Real, int N, int SI, int NS, int TC = 0> struct Stages {
-    using Cfg = PassCfg<Real, N, TC>;
+template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct Stages {
+    using Cfg = PassCfg<Real, N, TC, THR>;
     using C = typename Cfg::C;
     static constexpr int R = Cfg::plan.R[SI];
     static constexpr int NB = N / R;
@@ -276,7 +288,8 @@ template <typename Real, int N, int SI, int NS, int TC = 0> struct Stages {
         } else {
             simt(buf, tile, tw, gsrc, line, t, ok, conj);
         }
-        if constexpr (!LAST) Stages<Real, N, SI + 1, NS * R, TC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active);
+        if constexpr (!LAST)
+            Stages<Real, N, SI + 1, NS * R, TC, THR>::run(buf, tile, tw, gsrc, line, t, ok, conj, active);
     }
 
     __device__ __forceinline__ static void simt(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
@@ -331,9 +344,9 @@ template <typename Real, int N, int SI, int NS, int TC = 0> struct Stages {
 // The whole pass for one tile of lines.  Threads tid >= THREADS (a CTA shared
 // by several line lengths, see the grouped serving kernel) take part in the
 // barriers only.
-template <typename Real, int N, int TC>
+template <typename Real, int N, int TC, int THR = 0>
 __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned char *smem_raw, const int tid) {
-    using Cfg = PassCfg<Real, N, TC>;
+    using Cfg = PassCfg<Real, N, TC, THR>;
     using C = typename Cfg::C;
     C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
     C *tw = buf + Cfg::DATA;
@@ -396,7 +409,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
         __syncthreads();
     } else {
         const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
-        Stages<Real, N, 0, 1, TC>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0, active);
+        Stages<Real, N, 0, 1, TC, THR>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0, active);
     }
 
     // store role: thread owns line sl and writes k = k0, k0 + TL, ...
@@ -436,10 +449,10 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
 
 // ------------------------------------------------------------------ the kernel
 
-template <typename Real, int N, int TC = 0>
-__global__ void __launch_bounds__(PassCfg<Real, N, TC>::THREADS) fft_pass_kernel(const PassArgs a) {
+template <typename Real, int N, int TC = 0, int THR = 0>
+__global__ void __launch_bounds__(PassCfg<Real, N, TC, THR>::THREADS) fft_pass_kernel(const PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pass_tile<Real, N, TC>(a, blockIdx.x, smem_raw, threadIdx.x);
+    pass_tile<Real, N, TC, THR>(a, blockIdx.x, smem_raw, threadIdx.x);
 }
 
 }  // namespace mdfft

@@ -155,6 +155,24 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
 // Twiddle table of one pass (layout of tw_offset in fft_pass.cuh): entry
 // r * NS + k of stage s >= 1 is w_N^e, e = k r N / (NS R), w_N = exp(-2 pi i/N),
 // computed in FP64 with sincospi and rounded to the pass precision.
+}  // namespace
+
+void mdfft::detail::retile_pass(const mdfft_plan_s *p, int s, int lines, PassArgs *out, int64_t *ctas) {
+    const Pass &ps = p->pass[s];
+    PassArgs a = ps.args;
+    int Bg = 1, Bh = 1;
+    choose_tile(lines, a.Ng, a.Nh, p->elem, &Bg, &Bh);
+    a.Bg = Bg, a.Bh = Bh;
+    a.gblocks = (a.Ng + Bg - 1) / Bg;
+    a.hblocks = (a.Nh + Bh - 1) / Bh;
+    int64_t n = a.gblocks * a.hblocks;
+    for (int i = 0; i < a.nrest; ++i) n *= a.rest_count[i];
+    *out = a;
+    *ctas = n;
+}
+
+namespace {
+
 __global__ void twiddle_kernel(void *dst, int64_t n, mdfft::RadixPlan plan, int dbl) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= mdfft::tw_entries(plan)) return;
@@ -529,6 +547,89 @@ mdfft_status mdfft_exec_host(mdfft_plan_t p, const void *in_host, void *out_host
     e = cudaMemcpyAsync(out_host, dev_out, bytes, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     return MDFFT_OK;
+}
+
+mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int reps, mdfft_stream_t stream,
+                                 float *ms_before, float *ms_after) {
+    if (!p || !in || !out) return fail(MDFFT_E_ARG, "null argument");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan");
+    if (reps < 1) return fail(MDFFT_E_ARG, "reps must be >= 1");
+    const size_t bytes = (size_t)p->T * p->elem;
+    if (overlaps(in, out, bytes)) return fail(MDFFT_E_ARG, "in and out overlap");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(MDFFT_E_CUDA, "cudaEventCreate");
+    mdfft_status result = MDFFT_OK;
+    for (int s = 0; s < p->M && result == MDFFT_OK; ++s) {
+        Pass &ps = p->pass[s];
+        std::vector<PassKernel> variants{ps.k};
+        PassKernel k;
+        if (p->dt == MDFFT_C64)
+            for (int thr : {256, 512})
+                if (mdfft::find_pass_kernel_c64_thr(ps.n, thr, &k) && k.threads != ps.k.threads) variants.push_back(k);
+        float best_ms = -1.f, default_ms = -1.f;
+        Pass best = ps;
+        for (size_t v = 0; v < variants.size() && result == MDFFT_OK; ++v) {
+            const PassKernel &kv = variants[v];
+            if (kv.smem > 48 * 1024 &&
+                cudaFuncSetAttribute(kv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.smem) != cudaSuccess) {
+                result = fail(MDFFT_E_CUDA, "cudaFuncSetAttribute");
+                break;
+            }
+            // tile shapes: the default choice and powers of two along g
+            std::vector<std::pair<int, int>> tiles;
+            int bg0 = 1, bh0 = 1;
+            choose_tile(kv.lines, ps.args.Ng, ps.args.Nh, p->elem, &bg0, &bh0);
+            tiles.push_back({bg0, bh0});
+            for (int bg = kv.lines; bg >= 4; bg /= 2) {
+                if (bg > ps.args.Ng) continue;
+                const int bh = (int)std::min<int64_t>(ps.args.Nh, kv.lines / bg);
+                if (std::find(tiles.begin(), tiles.end(), std::make_pair(bg, bh)) == tiles.end())
+                    tiles.push_back({bg, bh});
+            }
+            for (size_t ti = 0; ti < tiles.size(); ++ti) {
+                Pass cand = ps;
+                cand.k = kv;
+                PassArgs &a = cand.args;
+                a.Bg = tiles[ti].first, a.Bh = tiles[ti].second;
+                a.gblocks = (a.Ng + a.Bg - 1) / a.Bg;
+                a.hblocks = (a.Nh + a.Bh - 1) / a.Bh;
+                cand.ctas = a.gblocks * a.hblocks;
+                for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
+                a.in = in;
+                a.out = out;
+                a.tw = (const char *)p->tw + ps.tw_offset;
+                a.scale = 1.0;
+                void *args[] = {&a};
+                cudaError_t e = cudaSuccess;
+                for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.ctas), dim3(kv.threads), args, kv.smem, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.ctas), dim3(kv.threads), args, kv.smem, st);
+                cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    result = cuda_fail(e, "autotune launch");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)reps;
+                if (v == 0 && ti == 0) default_ms = ms;
+                if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = cand;
+            }
+        }
+        if (result != MDFFT_OK) break;
+        best.args.in = nullptr, best.args.out = nullptr, best.args.tw = nullptr;
+        ps = best;
+        if (ms_before) ms_before[s] = default_ms;
+        if (ms_after) ms_after[s] = best_ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
 }
 
 mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {

@@ -1,0 +1,28 @@
+// pass_c64_tuned.cu -- complex64 pass kernels with a fixed CTA size (256 or 512
+// threads) for the common line lengths: the autotuner's alternatives to the
+// default launch shape of pass_c64.cu.
+#include "passes.h"
+
+namespace mdfft {
+
+template <int N, int THR> static PassKernel make_c64_thr() {
+    using Cfg = PassCfg<float, N, 0, THR>;
+    return PassKernel{(const void *)&fft_pass_kernel<float, N, 0, THR>, Cfg::THREADS, Cfg::LINES, Cfg::TL, Cfg::SMEM,
+                      Cfg::plan};
+}
+
+bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k) {
+    if (thr != 256 && thr != 512) return false;
+    switch (n) {
+#define MDFFT_CASE(N)                                                           \
+    case N:                                                                     \
+        *k = thr == 256 ? make_c64_thr<N, 256>() : make_c64_thr<N, 512>();      \
+        return true;
+        MDFFT_TUNED_LENGTHS(MDFFT_CASE)
+#undef MDFFT_CASE
+        default:
+            return false;
+    }
+}
+
+}  // namespace mdfft

@@ -18,6 +18,9 @@
     X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(240) X(256) X(320) X(384) X(480) X(512) X(640) \
         X(768) X(960) X(1024)
 
+// Line lengths with fixed-CTA-size variants for the autotuner.
+#define MDFFT_TUNED_LENGTHS(X) X(32) X(48) X(64) X(96) X(128) X(160) X(192) X(256) X(512)
+
 namespace mdfft {
 
 struct PassKernel {
@@ -30,5 +33,6 @@ struct PassKernel {
 bool find_pass_kernel_c64(int64_t n, PassKernel *k);
 bool find_pass_kernel_c128(int64_t n, PassKernel *k);
 bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k);  // tc: kTcFp16 or kTcBf16
+bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k);  // thr: 256 or 512 threads
 
 }  // namespace mdfft

@@ -35,6 +35,16 @@ mdfft_status plan_create(mdfft_plan_t *out, int M, const int64_t N[], int64_t P,
 }  // namespace detail
 }  // namespace mdfft
 
+struct mdfft_plan_s;
+
+namespace mdfft {
+namespace detail {
+// Launch arguments of pass s re-tiled for a CTA of `lines` lines (same
+// arithmetic per line, so the same results); *ctas receives the tile count.
+void retile_pass(const mdfft_plan_s *p, int s, int lines, PassArgs *a, int64_t *ctas);
+}  // namespace detail
+}  // namespace mdfft
+
 struct mdfft_plan_s {
     int M = 0;
     int64_t N[MDFFT_MAX_DIMS] = {0};

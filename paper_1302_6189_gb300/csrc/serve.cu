@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -32,8 +33,8 @@ namespace mdfft {
 namespace serve {
 
 constexpr int kMaxItems = 512;  // passes per step
-constexpr int kSlots = 4;       // tables (and graphs) in flight
-constexpr int kThreads = 512;   // CTA size of the persistent kernel
+constexpr int kSlots = 8;       // tables (and graphs) in flight
+constexpr int kThreads = 256;   // CTA size of the persistent kernel (every length uses all of it)
 
 // line lengths the persistent kernel carries (complex64); other lengths run
 // as separate launches of their own pass kernel within the same step
@@ -54,14 +55,28 @@ struct Table {
     Item items[kMaxItems];
 };
 
-template <int N> constexpr size_t smem_of() { return PassCfg<float, N, 0>::SMEM; }
-template <int N> constexpr int threads_of() { return PassCfg<float, N, 0>::THREADS; }
+template <int N> using ServeCfg = PassCfg<float, N, 0, kThreads>;
+template <int N> constexpr size_t smem_of() { return ServeCfg<N>::SMEM; }
+template <int N> constexpr int threads_of() { return ServeCfg<N>::THREADS; }
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 #define MDFFT_SMEM_MAX(i, N) cmax(smem_of<N>(),
 #define MDFFT_CLOSE(i, N) )
 constexpr size_t kSmem = MDFFT_SERVE_LENGTHS(MDFFT_SMEM_MAX) 0 MDFFT_SERVE_LENGTHS(MDFFT_CLOSE);
 #define MDFFT_THR_OK(i, N) static_assert(threads_of<N>() <= kThreads, "serve CTA too small");
 MDFFT_SERVE_LENGTHS(MDFFT_THR_OK)
+
+// tile lines of the serving configuration of each kind
+int lines_of_kind(int kind) {
+    switch (kind) {
+#define MDFFT_LINES(i, N) \
+    case i:               \
+        return ServeCfg<N>::LINES;
+        MDFFT_SERVE_LENGTHS(MDFFT_LINES)
+#undef MDFFT_LINES
+        default:
+            return 0;
+    }
+}
 
 int kind_of(int64_t n) {
     switch (n) {
@@ -75,31 +90,45 @@ int kind_of(int64_t n) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) serve_kernel(const Table *tab) {
+__global__ void __launch_bounds__(kThreads, 4) serve_kernel(const Table *tab) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PassArgs args;
     const int n = tab->n;
     const int64_t total = tab->total;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        int lo = 0, hi = n - 1;  // last item whose first tile is <= t
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab->items[mid].start <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        const Item &it = tab->items[lo];
-        {  // the item's arguments into shared memory
-            const int *src = reinterpret_cast<const int *>(&it.args);
+    // chunks of kChunk consecutive tiles, dealt to the CTAs in turn: tiles of
+    // different line lengths even out across CTAs, and consecutive tiles of
+    // a chunk mostly belong to one item, so item lookups and argument copies
+    // are rare (items are in increasing tile order, so lookups only advance)
+    constexpr int kChunk = 4;
+    int cur = 0;
+    int64_t cur_start = 0, cur_end = n > 1 ? tab->items[1].start : total;  // item 0 starts at tile 0
+    int kind = -1;
+    for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < total; c0 += (int64_t)gridDim.x * kChunk)
+        for (int64_t t = c0; t < c0 + kChunk && t < total; ++t) {
+        if (t >= cur_end || kind < 0) {
+            if (t >= cur_end) {  // binary search over the items after cur: last one starting <= t
+                int lo = cur + 1, hi = n - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (tab->items[mid].start <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                cur = lo;
+                cur_start = tab->items[cur].start;
+                cur_end = cur + 1 < n ? tab->items[cur + 1].start : total;
+            }
+            __syncthreads();  // every thread is done with the previous arguments
+            const int *src = reinterpret_cast<const int *>(&tab->items[cur].args);
             int *dst = reinterpret_cast<int *>(&args);
             for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+            kind = tab->items[cur].kind;
+            __syncthreads();
         }
-        const int kind = it.kind;
-        const int64_t local = t - it.start;
-        __syncthreads();
+        const int64_t local = t - cur_start;
         switch (kind) {
-#define MDFFT_RUN(i, N)                                            \
-    case i:                                                        \
-        pass_tile<float, N, 0>(args, local, smem, threadIdx.x); \
+#define MDFFT_RUN(i, N)                                                  \
+    case i:                                                              \
+        pass_tile<float, N, 0, kThreads>(args, local, smem, threadIdx.x); \
         break;
             MDFFT_SERVE_LENGTHS(MDFFT_RUN)
 #undef MDFFT_RUN
@@ -171,6 +200,7 @@ struct Slot {
     Table *dev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy = nullptr;  // the table copy node (its size follows the step's item count)
     cudaEvent_t done = nullptr;
     bool busy = false;
     std::vector<Request *> finishing;
@@ -181,8 +211,15 @@ struct Slot {
 
 using namespace mdfft::serve;
 
+struct ServePass {  // a plan's pass re-tiled for the persistent kernel
+    PassArgs args;
+    int64_t ctas;
+    int kind;
+};
+
 struct mdfft_server_s {
     size_t budget = 0, in_use = 0;
+    std::map<mdfft_plan_t, std::vector<ServePass>> retiled;
     int max_inflight = 0;
     int64_t P = 64;
     cudaStream_t stream = nullptr, capture = nullptr;
@@ -195,6 +232,7 @@ struct mdfft_server_s {
     std::vector<Request *> inflight;
     std::unordered_map<int64_t, Request *> requests;
     int64_t next_id = 1;
+    int depth = 2;  // steps in flight on the GPU at most; arrivals in between join the next step
     Slot slots[kSlots];
     int next_slot = 0;
     cudaEvent_t t0 = nullptr;
@@ -215,6 +253,15 @@ mdfft_status capture_graphs(mdfft_server_t s) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        size_t nn = 0;
+        cudaGraphGetNodes(sl.graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(sl.graph, nodes.data(), &nn);
+        sl.copy = nullptr;
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeMemcpy) sl.copy = nd;
+        }
     }
     return MDFFT_OK;
 }
@@ -254,6 +301,13 @@ mdfft_status get_plan(mdfft_server_t s, int M, const int64_t *N, mdfft_plan_t *o
     mdfft_status st = mdfft::detail::plan_create(&p, M, N, std::min<int64_t>(s->P, T), nullptr, MDFFT_C64, 0, false);
     if (st != MDFFT_OK) return st;
     s->plans[key] = p;
+    std::vector<ServePass> rt(M);
+    for (int q = 0; q < M; ++q) {
+        rt[q].kind = kind_of(p->pass[q].n);
+        rt[q].ctas = 0;
+        if (rt[q].kind >= 0) mdfft::detail::retile_pass(p, q, lines_of_kind(rt[q].kind), &rt[q].args, &rt[q].ctas);
+    }
+    s->retiled[p] = rt;
     *out = p;
     return MDFFT_OK;
 }
@@ -386,6 +440,9 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     for (Request *r : s->inflight)
         if (r->next_pass < r->plan->M) todo.push_back(r);
     if (todo.empty()) return MDFFT_OK;
+    int busy = 0;
+    for (const Slot &b : s->slots) busy += b.busy;
+    if (busy >= s->depth) return MDFFT_OK;  // the GPU has enough queued: let more work gather
     Slot &sl = s->slots[s->next_slot];
     if (sl.busy) {  // its table may still be in use: wait for that step
         cudaError_t e = cudaEventSynchronize(sl.done);
@@ -400,15 +457,17 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         if (n >= kMaxItems) break;
         const int pass = r->next_pass;
         const PassArgs a = pass_args(s, r, pass);
-        const int kind = kind_of(r->plan->pass[pass].n);
-        if (kind < 0) {
+        const ServePass &sp = s->retiled[r->plan][pass];
+        if (sp.kind < 0) {
             separate.push_back({r, a});
-        } else {
+        } else {  // the same pass re-tiled for the persistent kernel's CTA
             Item &it = tab->items[n++];
-            it.args = a;
+            it.args = sp.args;
+            it.args.in = a.in, it.args.out = a.out, it.args.tw = a.tw;
+            it.args.conj = a.conj, it.args.scale = a.scale;
             it.start = total;
-            it.kind = kind;
-            total += r->plan->pass[pass].ctas;
+            it.kind = sp.kind;
+            total += sp.ctas;
         }
         r->next_pass++;
         if (r->next_pass == r->plan->M) {
@@ -420,6 +479,11 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     tab->total = total;
     cudaError_t e = cudaSuccess;
     if (n > 0) {
+        if (sl.copy) {  // copy only the header and the items of this step
+            const size_t used = offsetof(Table, items) + (size_t)n * sizeof(Item);
+            e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy, sl.dev, sl.host, used, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphExecMemcpyNodeSetParams1D");
+        }
         e = cudaGraphLaunch(sl.exec, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
         s->stats.graph_launches++;
@@ -439,6 +503,19 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     s->next_slot = (s->next_slot + 1) % kSlots;
     s->stats.steps++;
     if (launched) *launched = 1;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_run(mdfft_server_t s, int max_steps, int *steps) {
+    if (!s) return fail(MDFFT_E_ARG, "null server");
+    int n = 0;
+    for (; n < max_steps; ++n) {
+        int launched = 0;
+        mdfft_status st = mdfft_server_step(s, &launched);
+        if (st != MDFFT_OK) return st;
+        if (!launched) break;
+    }
+    if (steps) *steps = n;
     return MDFFT_OK;
 }
 
@@ -472,13 +549,15 @@ mdfft_status mdfft_server_drain(mdfft_server_t s) {
         int launched = 0;
         mdfft_status st = mdfft_server_step(s, &launched);
         if (st != MDFFT_OK) return st;
-        if (!launched) {  // nothing left to launch: wait for the steps in flight
-            for (Slot &sl : s->slots)
-                if (sl.busy) {
-                    cudaError_t e = cudaEventSynchronize(sl.done);
-                    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-                    resolve_slot(s, sl);
-                }
+        if (!launched) {  // nothing to launch until a step completes: wait for the oldest one only
+            for (int k = 0; k < kSlots; ++k) {
+                Slot &sl = s->slots[(s->next_slot + k) % kSlots];
+                if (!sl.busy) continue;
+                cudaError_t e = cudaEventSynchronize(sl.done);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+                resolve_slot(s, sl);
+                break;
+            }
         }
     }
     return MDFFT_OK;
@@ -503,6 +582,12 @@ mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas) {
     s->grid = ctas;
     s->stats.grid_ctas = ctas;
     return capture_graphs(s);
+}
+
+mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth) {
+    if (!s || depth < 1 || depth > kSlots) return fail(MDFFT_E_ARG, "depth must be in [1, 8]");
+    s->depth = depth;
+    return MDFFT_OK;
 }
 
 mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out) {

@@ -62,6 +62,8 @@ SIGNATURES = {
     "mdfft_pass_times": (c_int, [c_void_p, P_(ctypes.c_float), c_int, P_(c_int)]),
     "mdfft_exec_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_pass_describe": (c_int, [c_void_p, c_int, P_(MdfftPassInfo)]),
+    "mdfft_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, P_(ctypes.c_float),
+                                    P_(ctypes.c_float)]),
     "mdfft_workspace_size": (c_int, [c_void_p, P_(c_size_t)]),
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_supported_length": (c_int, [i64, c_int]),
@@ -71,11 +73,13 @@ SIGNATURES = {
     "mdfft_server_create": (c_int, [P_(c_void_p), c_size_t, c_int, i64, c_void_p]),
     "mdfft_server_submit": (c_int, [c_void_p, c_int, P_(i64), c_void_p, c_void_p, c_int, c_int, P_(i64)]),
     "mdfft_server_step": (c_int, [c_void_p, P_(c_int)]),
+    "mdfft_server_run": (c_int, [c_void_p, c_int, P_(c_int)]),
     "mdfft_server_poll": (c_int, [c_void_p, i64, P_(c_int), P_(ctypes.c_double)]),
     "mdfft_server_release": (c_int, [c_void_p, i64]),
     "mdfft_server_drain": (c_int, [c_void_p]),
     "mdfft_server_reset_clock": (c_int, [c_void_p]),
     "mdfft_server_set_grid": (c_int, [c_void_p, c_int]),
+    "mdfft_server_set_depth": (c_int, [c_void_p, c_int]),
     "mdfft_server_get_stats": (c_int, [c_void_p, P_(MdfftServerStats)]),
     "mdfft_server_destroy": (c_int, [c_void_p]),
 }
@@ -206,6 +210,13 @@ def mdfft_pass_describe(plan, s):
     return {f: getattr(info, f) for f, _ in MdfftPassInfo._fields_}
 
 
+def mdfft_plan_autotune(plan, in_ptr, out_ptr, reps, stream, M):
+    before, after = (ctypes.c_float * M)(), (ctypes.c_float * M)()
+    _check(_lib.mdfft_plan_autotune(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(reps), c_void_p(stream),
+                                    before, after), "mdfft_plan_autotune")
+    return list(before), list(after)
+
+
 def mdfft_workspace_size(plan):
     n = c_size_t()
     _check(_lib.mdfft_workspace_size(plan, ctypes.byref(n)), "mdfft_workspace_size")
@@ -257,6 +268,12 @@ def mdfft_server_step(server):
     return bool(launched.value)
 
 
+def mdfft_server_run(server, max_steps):
+    n = c_int()
+    _check(_lib.mdfft_server_run(server, int(max_steps), ctypes.byref(n)), "mdfft_server_run")
+    return n.value
+
+
 def mdfft_server_poll(server, request_id):
     done, ms = c_int(), ctypes.c_double()
     _check(_lib.mdfft_server_poll(server, int(request_id), ctypes.byref(done), ctypes.byref(ms)),
@@ -278,6 +295,10 @@ def mdfft_server_reset_clock(server):
 
 def mdfft_server_set_grid(server, ctas):
     _check(_lib.mdfft_server_set_grid(server, int(ctas)), "mdfft_server_set_grid")
+
+
+def mdfft_server_set_depth(server, depth):
+    _check(_lib.mdfft_server_set_depth(server, int(depth)), "mdfft_server_set_depth")
 
 
 def mdfft_server_get_stats(server):
@@ -373,6 +394,13 @@ class Plan:
                         dev_out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
         return out_host
 
+    def autotune(self, x, scratch, reps=10, stream=None):
+        """Pick the fastest kernel variant and tile shape per pass; returns
+        (ms per pass before, after).  x is only read; scratch is overwritten."""
+        self._check_tensor(x, "input")
+        self._check_tensor(scratch, "scratch")
+        return mdfft_plan_autotune(self.handle, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream), self.M)
+
     def workspace_bytes(self):
         return mdfft_workspace_size(self.handle)
 
@@ -418,6 +446,9 @@ class Server:
     def step(self):
         return mdfft_server_step(self.handle)
 
+    def run(self, max_steps=4):
+        return mdfft_server_run(self.handle, max_steps)
+
     def poll(self, rid):
         return mdfft_server_poll(self.handle, rid)
 
@@ -432,6 +463,9 @@ class Server:
 
     def set_grid(self, ctas):
         mdfft_server_set_grid(self.handle, ctas)
+
+    def set_depth(self, depth):
+        mdfft_server_set_depth(self.handle, depth)
 
     def stats(self):
         return mdfft_server_get_stats(self.handle)

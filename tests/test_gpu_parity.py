@@ -271,3 +271,18 @@ def test_512cubed_sampled_outputs():
     lhs = float(np.sum(np.abs(yh.astype(np.complex128)) ** 2))
     rhs = float(x.size * np.sum(np.abs(x128) ** 2))
     assert abs(lhs - rhs) <= 1e-5 * rhs
+
+
+def test_autotune_keeps_results_bit_identical():
+    for shape, dt in [((256, 128, 64), "c64"), ((96, 48, 160), "c64"), ((64, 32, 48), "c128")]:
+        x = torch.from_numpy(si.uniform_complex(shape, 95, NP[dt])).to(DEV)
+        with md.Plan(shape, 16, None, dt) as plan:
+            before = plan.exec(x)
+            scratch = torch.empty_like(x)
+            ms0, ms1 = plan.autotune(x, scratch, reps=3)
+            assert all(b <= a * 1.05 + 1e-3 for a, b in zip(ms0, ms1))  # never picks a slower configuration
+            after = plan.exec(x)
+            torch.cuda.synchronize()
+            assert torch.equal(before, after), shape
+            for d in plan.describe():
+                assert d["tile_g"] * d["tile_h"] * (d["threads"] // max(1, d["threads"])) >= 1
