@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
     ap.add_argument("--serving-only", type=int, default=0, metavar="REQUESTS",
                     help="run only the serving study with this many requests and print it")
+    ap.add_argument("--serving-budget-gb", type=float, default=40.0)
     return ap.parse_args()
 
 
@@ -608,7 +609,8 @@ def main():
     if args.serving_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"serving": serving_study(torch.device("cuda", 0), n=args.serving_only)}), flush=True)
+        print(json.dumps({"serving": serving_study(torch.device("cuda", 0), n=args.serving_only,
+                                                   budget=args.serving_budget_gb * 1e9)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "smem_layout.h"
+
 namespace mdfft {
 
 constexpr int kMaxTileDims = 8;
@@ -138,8 +140,12 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int LINES = lines_for();
     static_assert(TL * LINES <= kMaxThreads && (TL * LINES) % 32 == 0, "CTA shape");
     static constexpr int THREADS = TL * LINES;
-    static constexpr int PADN = N + N / 16 + 1;  // padded line stride in the stage buffer
-    static constexpr int TROW = LINES + 1;       // padded row of the transposed tile
+    // shared-memory padding (the bank-conflict-free choice of smem_layout.h
+    // for complex64; tensor-core and complex128 configurations use the default)
+    static constexpr SmemLayout LAY = (sizeof(Real) == 4 && TC == 0) ? smem_layout_c64(N, THR) : SmemLayout{16, 1, 1};
+    static constexpr int PADG = LAY.g;                // pad(i) = i + i / PADG
+    static constexpr int PADN = N + N / PADG + LAY.pe;  // line stride of the stage buffer
+    static constexpr int TROW = LINES + LAY.te;         // row of the transposed tile
     static constexpr int DATA = LINES * PADN > N * TROW ? LINES * PADN : N * TROW;
     static constexpr int TWN = tw_entries(plan) > 0 ? tw_entries(plan) : 1;  // twiddle entries
     static constexpr int BFRAG = TC ? 1024 * 4 / (int)sizeof(C) : 0;  // tensor-core B fragments (in C units)
@@ -252,6 +258,7 @@ template <int R, typename C> __device__ __forceinline__ void dft(C (&v)[R]) {
 }
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+template <int G> __device__ __forceinline__ int padg(int i) { return i + i / G; }
 
 }  // namespace mdfft
 
@@ -306,7 +313,7 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct 
                         if (conj) x.y = -x.y;
                         v[i][r] = x;
                     } else {
-                        v[i][r] = buf[line * Cfg::PADN + pad16(j + r * NB)];
+                        v[i][r] = buf[line * Cfg::PADN + padg<Cfg::PADG>(j + r * NB)];
                     }
                 } else {
                     v[i][r] = C{0, 0};
@@ -330,7 +337,7 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct 
                     if constexpr (LAST) {
                         tile[(base + r * NS) * Cfg::TROW + line] = v[i][r];
                     } else {
-                        buf[line * Cfg::PADN + pad16(base + r * NS)] = v[i][r];
+                        buf[line * Cfg::PADN + padg<Cfg::PADG>(base + r * NS)] = v[i][r];
                     }
                 }
             }
@@ -395,7 +402,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
                 if (l < a.Bg * a.Bh && g0 + bg < a.Ng && h0 + bh < a.Nh) {
                     C x = in[lbase[l] + i];
                     if (a.conj) x.y = -x.y;
-                    buf[l * Cfg::PADN + pad16(i)] = x;
+                    buf[l * Cfg::PADN + padg<Cfg::PADG>(i)] = x;
                 }
             }
         }
