@@ -67,6 +67,9 @@ typedef enum {
 /* mdfft_plan flags */
 #define MDFFT_PLAN_HOST_ONLY 0x1u /* planner only: no device memory; exec refused */
 #define MDFFT_PLAN_INPLACE 0x2u   /* allow in_dev == out_dev (one more workspace) */
+#define MDFFT_PLAN_PERSISTENT 0x4u /* complex64: use the persistent bulk-copy pipelined pass kernel
+                                      wherever one is built (even lengths <= 512); arrays must then be
+                                      16-byte aligned */
 
 /*
  * mdfft_plan -- build a plan for the M-D FFT of dims N[0..M) with Np = P
@@ -192,8 +195,10 @@ mdfft_status mdfft_exec_host(mdfft_plan_t plan, const void *in_host, void *out_h
 typedef struct {
     int64_t line_length;
     int tile_g, tile_h, threads, smem_bytes;
-    int64_t ctas;
+    int64_t ctas;      /* tiles */
     int fft_axis, store_axis;
+    int64_t grid;      /* CTAs launched (= ctas unless persistent) */
+    int persistent;    /* 0: one CTA per tile; 1 or 2: persistent kernel with that many landing buffers */
 } mdfft_pass_info;
 mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out);
 
@@ -202,7 +207,10 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * its line length (the default launch shape and, for complex64 lengths 32,
  * 48, 64, 96, 128, 160, 192, 256, 512, fixed 256- and 512-thread CTAs) with
  * several tile shapes (lines along the output's fastest axis x lines along
- * the next axis), `reps` launches each, and keeps the fastest.  Tiling never
+ * the next axis), `reps` launches each, and keeps the fastest.  For even
+ * complex64 lengths up to 512 the candidates include a persistent kernel
+ * that streams tiles through shared memory with bulk (TMA) copies; a plan
+ * using it needs 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).  Tiling never
  * changes results.  in_dev (T elements, only read) and out_dev (T elements,
  * overwritten with scratch) are the caller's; the call synchronises `stream`.
  * ms_before / ms_after (M entries each, may be NULL) receive the mean pass
@@ -210,6 +218,12 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  */
 mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *out_dev, int reps, mdfft_stream_t stream,
                                  float *ms_before, float *ms_after);
+
+/* Waits for the device and reports whether a pass kernel of this plan gave up
+ * a bounded wait since the last check (MDFFT_E_TIMEOUT; the affected output
+ * is incomplete).  Only the persistent pipelined kernels that
+ * mdfft_plan_autotune may select wait on the device. */
+mdfft_status mdfft_plan_check(mdfft_plan_t plan);
 
 /* Device workspace the plan owns, in bytes (0 for host-only plans). */
 mdfft_status mdfft_workspace_size(mdfft_plan_t plan, size_t *bytes);

@@ -54,6 +54,8 @@ struct PassArgs {
     int64_t out_sh, out_sf;         // output strides of h and f (g has output stride 1)
     int conj;                       // 1: inverse
     double scale;                   // multiplies every stored value
+    int64_t ntiles;                 // tiles of the pass (persistent kernels walk them)
+    int *err;                       // persistent kernels: set to 1 if a bounded wait gave up (may be null)
     unsigned long long *moved;      // count mode: points whose owner changes (null: off)
     unsigned long long *split;      // count mode: split-line amount of the input layout
     OwnerMap own_in, own_out;
@@ -276,8 +278,12 @@ __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
 // One Stockham stage with radix R after NS points already combined.
 // Butterfly j (< N/R) reads x[j + r N/R], applies w_{NS R}^{(j mod NS) r},
 // does DFT_R and writes y[(j / NS) NS R + j mod NS + r NS].
-template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct Stages {
+// SRC selects where the first stage reads: -1 the default of the
+// configuration (HBM directly when DIRECT, else the staged tile), 2 a landing
+// buffer in shared memory holding the tile's lines unpadded (gsrc = the line).
+template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC = -1> struct Stages {
     using Cfg = PassCfg<Real, N, TC, THR>;
+    static constexpr int SRC0 = SRC >= 0 ? SRC : (Cfg::DIRECT ? 1 : 0);
     using C = typename Cfg::C;
     static constexpr int R = Cfg::plan.R[SI];
     static constexpr int NB = N / R;
@@ -286,17 +292,25 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct 
     static constexpr bool LAST = SI == Cfg::plan.S - 1;
     static constexpr int TWOFF = tw_offset(Cfg::plan, SI);
 
-    // gsrc: this thread's line in HBM (first stage, direct loads) or null
+    struct NoHook {
+        __device__ __forceinline__ void operator()() const {}
+    };
+
+    // gsrc: this thread's line in HBM (first stage, direct loads) or null.
+    // after_first() runs once the first stage is done with its source (all
+    // threads, after the stage's closing barrier).
+    template <class Hook = NoHook>
     __device__ __forceinline__ static void run(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
-                                               bool ok, bool conj, bool active) {
+                                               bool ok, bool conj, bool active, const Hook &after_first = Hook()) {
         if constexpr (TC != 0 && R == 16) {
             tc_radix16_stage<TC, N, Cfg::LINES, Cfg::THREADS, Cfg::PADN, Cfg::TROW, NS, LAST>(
                 buf, tile, tw + TWOFF, reinterpret_cast<const uint32_t *>(tw + Cfg::TWN), active);
         } else {
             simt(buf, tile, tw, gsrc, line, t, ok, conj);
         }
+        if constexpr (FIRST) after_first();
         if constexpr (!LAST)
-            Stages<Real, N, SI + 1, NS * R, TC, THR>::run(buf, tile, tw, gsrc, line, t, ok, conj, active);
+            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active);
     }
 
     __device__ __forceinline__ static void simt(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
@@ -308,8 +322,12 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct 
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if ((NB % Cfg::TL == 0 || j < NB) && ok) {
-                    if constexpr (FIRST && Cfg::DIRECT) {
+                    if constexpr (FIRST && SRC0 == 1) {
                         C x = __ldg(gsrc + j + r * NB);
+                        if (conj) x.y = -x.y;
+                        v[i][r] = x;
+                    } else if constexpr (FIRST && SRC0 == 2) {
+                        C x = gsrc[j + r * NB];
                         if (conj) x.y = -x.y;
                         v[i][r] = x;
                     } else {
@@ -320,7 +338,7 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct 
                 }
             }
         }
-        if constexpr (!(FIRST && Cfg::DIRECT)) __syncthreads();  // all reads of buf before any write
+        if constexpr (!(FIRST && SRC0 != 0)) __syncthreads();  // all reads of buf before any write
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int j = t + i * Cfg::TL;
@@ -348,84 +366,48 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0> struct 
 
 // ------------------------------------------------------------------ one tile
 
-// The whole pass for one tile of lines.  Threads tid >= THREADS (a CTA shared
-// by several line lengths, see the grouped serving kernel) take part in the
-// barriers only.
-template <typename Real, int N, int TC, int THR = 0>
-__device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned char *smem_raw, const int tid) {
-    using Cfg = PassCfg<Real, N, TC, THR>;
-    using C = typename Cfg::C;
-    C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
-    C *tw = buf + Cfg::DATA;
-    int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);  // input offset of each tile line
-    const bool active = tid < Cfg::THREADS;
+// Tile t of a pass: where its lines start in the input and output arrays and
+// its first line along g and h.
+struct TileCoord {
+    int64_t in_base, out_base, g0, h0;
+};
 
-    const C *in = reinterpret_cast<const C *>(a.in);
-    C *out = reinterpret_cast<C *>(a.out);
-    const C *gtw = reinterpret_cast<const C *>(a.tw);
-
-    // tile coordinates
+__device__ __forceinline__ TileCoord tile_coords(const PassArgs &a, int64_t t) {
+    TileCoord c;
     const int64_t gb = t % a.gblocks;
     t /= a.gblocks;
     const int64_t hb = t % a.hblocks;
     t /= a.hblocks;
-    const int64_t g0 = gb * a.Bg, h0 = hb * a.Bh;
-    int64_t in_base = g0 * a.in_sg + h0 * a.in_sh;
-    int64_t out_base = g0 + h0 * a.out_sh;
+    c.g0 = gb * a.Bg, c.h0 = hb * a.Bh;
+    c.in_base = c.g0 * a.in_sg + c.h0 * a.in_sh;
+    c.out_base = c.g0 + c.h0 * a.out_sh;
     for (int i = 0; i < a.nrest; ++i) {
-        const int64_t c = t % a.rest_count[i];
+        const int64_t q = t % a.rest_count[i];
         t /= a.rest_count[i];
-        in_base += c * a.rest_in[i];
-        out_base += c * a.rest_out[i];
+        c.in_base += q * a.rest_in[i];
+        c.out_base += q * a.rest_out[i];
     }
+    return c;
+}
 
-    if (active) {
-        for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
-        if constexpr (TC != 0) tc_build_bfrag<TC, Cfg::THREADS>(reinterpret_cast<uint32_t *>(tw + Cfg::TWN), tid);
-        if (tid < Cfg::LINES) {
-            const int bg = tid % a.Bg, bh = tid / a.Bg;
-            lbase[tid] = in_base + bg * a.in_sg + bh * a.in_sh;
-        }
-    }
-    __syncthreads();
-
-    // FFT role: thread (line, t) with t fastest
-    const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
-    const int fbg = line % a.Bg, fbh = line / a.Bg;
-    const bool fok = active && line < a.Bg * a.Bh && g0 + fbg < a.Ng && h0 + fbh < a.Nh;
-
-    if constexpr (!Cfg::DIRECT) {  // stage the whole tile through shared memory
-        if (active) {
-            for (int e = tid; e < Cfg::LINES * N; e += Cfg::THREADS) {
-                const int l = e / N, i = e % N;
-                const int bg = l % a.Bg, bh = l / a.Bg;
-                if (l < a.Bg * a.Bh && g0 + bg < a.Ng && h0 + bh < a.Nh) {
-                    C x = in[lbase[l] + i];
-                    if (a.conj) x.y = -x.y;
-                    buf[l * Cfg::PADN + padg<Cfg::PADG>(i)] = x;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if constexpr (Cfg::plan.S == 0) {  // length-1 lines: the DFT is the identity
-        C v = C{0, 0};
-        if (active) v = buf[line * Cfg::PADN];
-        __syncthreads();
-        if (active) buf[line] = v;  // tile[k = 0][line]
-        __syncthreads();
-    } else {
-        const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
-        Stages<Real, N, 0, 1, TC, THR>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0, active);
-    }
-
-    // store role: thread owns line sl and writes k = k0, k0 + TL, ...
+// Store role: the transposed tile in shared memory (buf as [k][TROW]) goes
+// to the output layout; every thread owns line sl and writes k = k0, k0 + TL,
+// ...  so a warp writes runs of Bg consecutive elements.  Count mode adds the
+// points whose owner changes and the split-line amount (lbase: input offset
+// of every tile line).
+template <typename Real, int N, int TC, int THR>
+__device__ __forceinline__ void store_tile(const PassArgs &a, const typename PassCfg<Real, N, TC, THR>::C *buf,
+                                           const int64_t *lbase, const TileCoord &c, const int tid) {
+    using Cfg = PassCfg<Real, N, TC, THR>;
+    using C = typename Cfg::C;
+    C *out = reinterpret_cast<C *>(a.out);
+    const bool active = tid < Cfg::THREADS;
     const int sl = tid % Cfg::LINES, k0 = tid / Cfg::LINES;
     const int sbg = sl % a.Bg, sbh = sl / a.Bg;
-    const bool sok = active && sl < a.Bg * a.Bh && g0 + sbg < a.Ng && h0 + sbh < a.Nh;
+    const bool sok = active && sl < a.Bg * a.Bh && c.g0 + sbg < a.Ng && c.h0 + sbh < a.Nh;
     unsigned long long moved = 0, split = 0;
     if (sok) {
-        const int64_t obase = out_base + sbh * a.out_sh + sbg;
+        const int64_t obase = c.out_base + sbh * a.out_sh + sbg;
         const Real sc = (Real)a.scale;
 #pragma unroll 4
         for (int k = k0; k < N; k += Cfg::TL) {
@@ -452,6 +434,64 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
             if (split) atomicAdd(a.split, split);
         }
     }
+}
+
+// The whole pass for one tile of lines.  Threads tid >= THREADS (a CTA shared
+// by several line lengths, see the grouped serving kernel) take part in the
+// barriers only.
+template <typename Real, int N, int TC, int THR = 0>
+__device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned char *smem_raw, const int tid) {
+    using Cfg = PassCfg<Real, N, TC, THR>;
+    using C = typename Cfg::C;
+    C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
+    C *tw = buf + Cfg::DATA;
+    int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);  // input offset of each tile line
+    const bool active = tid < Cfg::THREADS;
+
+    const C *in = reinterpret_cast<const C *>(a.in);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+    const TileCoord c = tile_coords(a, t);
+
+    if (active) {
+        for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
+        if constexpr (TC != 0) tc_build_bfrag<TC, Cfg::THREADS>(reinterpret_cast<uint32_t *>(tw + Cfg::TWN), tid);
+        if (tid < Cfg::LINES) {
+            const int bg = tid % a.Bg, bh = tid / a.Bg;
+            lbase[tid] = c.in_base + bg * a.in_sg + bh * a.in_sh;
+        }
+    }
+    __syncthreads();
+
+    // FFT role: thread (line, t) with t fastest
+    const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
+    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    const bool fok = active && line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh;
+
+    if constexpr (!Cfg::DIRECT) {  // stage the whole tile through shared memory
+        if (active) {
+            for (int e = tid; e < Cfg::LINES * N; e += Cfg::THREADS) {
+                const int l = e / N, i = e % N;
+                const int bg = l % a.Bg, bh = l / a.Bg;
+                if (l < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
+                    C x = in[lbase[l] + i];
+                    if (a.conj) x.y = -x.y;
+                    buf[l * Cfg::PADN + padg<Cfg::PADG>(i)] = x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (Cfg::plan.S == 0) {  // length-1 lines: the DFT is the identity
+        C v = C{0, 0};
+        if (active) v = buf[line * Cfg::PADN];
+        __syncthreads();
+        if (active) buf[line] = v;  // tile[k = 0][line]
+        __syncthreads();
+    } else {
+        const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
+        Stages<Real, N, 0, 1, TC, THR>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0, active);
+    }
+    store_tile<Real, N, TC, THR>(a, buf, lbase, c, tid);
 }
 
 // ------------------------------------------------------------------ the kernel

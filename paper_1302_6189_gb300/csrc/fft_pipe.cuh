@@ -1,0 +1,171 @@
+// fft_pipe.cuh -- persistent pass kernel with a bulk-copy (TMA) load pipeline.
+//
+// Same pass as fft_pass_kernel (Fig. 4 step + the transpose after it), but
+// each CTA walks tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... and keeps
+// the input of the next tiles in flight while it computes and stores the
+// current one.  One or two landing buffers in shared memory take a tile's
+// lines unpadded; warp 0 fills them with one cp.async.bulk (1-D TMA) copy per
+// line, completing on the buffer's mbarrier with the tile's byte count.  A
+// tile is consumed by the first Stockham stage straight from its landing
+// buffer, which is refilled right after that stage with the tile NBUF steps
+// ahead, while the rest of the FFT and the store of the current tile run.
+//
+// Waits on an mbarrier are bounded (2 s of %globaltimer); a CTA whose wait
+// gives up sets *err, waits (bounded) for its other copies, and exits with
+// the whole CTA; the host reports MDFFT_E_TIMEOUT.
+//
+// Requirements (checked on the host): complex64, even N (lines are whole
+// 16-byte units), input 16-byte aligned.
+#pragma once
+
+#include "fft_pass.cuh"
+
+namespace mdfft {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbarrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true if the phase of the given parity completed within limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+template <int N, int NBUF> struct PipeCfg {
+    using Cfg = PassCfg<float, N, 0, 0>;
+    static_assert(N % 2 == 0, "bulk copies need lines of whole 16-byte units");
+    static_assert(NBUF == 1 || NBUF == 2, "one or two landing buffers");
+    static constexpr int LAND = Cfg::LINES * N;  // complex64 per landing buffer
+    static constexpr size_t HEAD = 128;          // the mbarriers, padded
+    static constexpr size_t SMEM = HEAD + NBUF * (size_t)LAND * sizeof(float2) + Cfg::SMEM;
+    static constexpr uint64_t kWaitLimitNs = 2000000000ull;
+};
+
+// Warp 0: arm barrier b with the byte count of tile t and copy its valid lines.
+template <int N>
+__device__ __forceinline__ void pipe_issue(const PassArgs &a, int64_t t, float2 *land, uint64_t *bar, int lane) {
+    using Cfg = PassCfg<float, N, 0, 0>;
+    const TileCoord c = tile_coords(a, t);
+    const int64_t vg = a.Ng - c.g0 < a.Bg ? a.Ng - c.g0 : a.Bg;
+    const int64_t vh = a.Nh - c.h0 < a.Bh ? a.Nh - c.h0 : a.Bh;
+    if (lane == 0) {
+        fence_proxy_async_shared();  // earlier generic reads of this buffer before the async writes
+        mbar_arrive_expect_tx(bar, (uint32_t)(vg * vh * N * sizeof(float2)));
+    }
+    __syncwarp();
+    const float2 *in = reinterpret_cast<const float2 *>(a.in);
+    for (int l = lane; l < Cfg::LINES; l += 32) {
+        const int bg = l % a.Bg, bh = l / a.Bg;
+        if (l < a.Bg * a.Bh && bg < vg && bh < vh)
+            bulk_copy_g2s(land + (size_t)l * N, in + c.in_base + bg * a.in_sg + bh * a.in_sh,
+                          (uint32_t)(N * sizeof(float2)), bar);
+    }
+}
+
+// NBUF landing buffers: tile k of this CTA lands in buffer k % NBUF; right
+// after the first stage has read it, that buffer is refilled with tile
+// k + NBUF, so the copy overlaps the rest of tile k (and, with two buffers,
+// all of tile k + 1).
+template <int N, int NBUF>
+__global__ void __launch_bounds__(PassCfg<float, N, 0, 0>::THREADS) fft_pass_pipe_kernel(const PassArgs a) {
+    using Cfg = PassCfg<float, N, 0, 0>;
+    using P = PipeCfg<N, NBUF>;
+    using C = float2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    C *land = reinterpret_cast<C *>(smem_raw + P::HEAD);
+    unsigned char *work = smem_raw + P::HEAD + NBUF * (size_t)P::LAND * sizeof(C);
+    C *buf = reinterpret_cast<C *>(work);
+    C *tw = buf + Cfg::DATA;
+    int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t G = gridDim.x, ntiles = a.ntiles;
+
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+    for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
+    if (tid == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    if (warp == 0)
+        for (int b = 0; b < NBUF; ++b)
+            if ((int64_t)blockIdx.x + b * G < ntiles)
+                pipe_issue<N>(a, blockIdx.x + b * G, land + (size_t)b * P::LAND, &bar[b], lane);
+
+    const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
+    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += G, ++k) {
+        const int b = (int)(k % NBUF);
+        const uint32_t parity = (uint32_t)((k / NBUF) & 1);
+        const TileCoord c = tile_coords(a, t);
+        if (tid < Cfg::LINES) {
+            const int bg = tid % a.Bg, bh = tid / a.Bg;
+            lbase[tid] = c.in_base + bg * a.in_sg + bh * a.in_sh;
+        }
+        const bool ok = mbar_wait_bounded(&bar[b], parity, P::kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.err) atomicExch(a.err, 1);
+            // the other buffers may still be filling: give their copies a bounded chance to land
+            for (int o = 1; o < NBUF; ++o)
+                if (t + o * G < ntiles)
+                    mbar_wait_bounded(&bar[(k + o) % NBUF], (uint32_t)(((k + o) / NBUF) & 1), P::kWaitLimitNs);
+            return;
+        }
+        const bool fok = line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh;
+        C *mine = land + (size_t)b * P::LAND;
+        auto refill = [&]() {  // buffer b has been read by the first stage
+            if (warp == 0 && t + NBUF * G < ntiles) pipe_issue<N>(a, t + NBUF * G, mine, &bar[b], lane);
+        };
+        Stages<float, N, 0, 1, 0, 0, 2>::run(buf, buf, tw, mine + (size_t)line * N, line, tl, fok, a.conj != 0, true,
+                                             refill);
+        store_tile<float, N, 0, 0>(a, buf, lbase, c, tid);
+        __syncthreads();  // the tile region and lbase are rewritten by the next tile
+    }
+}
+
+}  // namespace mdfft

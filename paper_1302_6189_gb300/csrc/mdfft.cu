@@ -149,6 +149,7 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
+    ps.grid = ps.ctas;
     return MDFFT_OK;
 }
 
@@ -156,6 +157,15 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
 // r * NS + k of stage s >= 1 is w_N^e, e = k r N / (NS R), w_N = exp(-2 pi i/N),
 // computed in FP64 with sincospi and rounded to the pass precision.
 }  // namespace
+
+int64_t mdfft::detail::wave_ctas(const PassKernel &k) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (k.smem > 48 * 1024) cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.fn, k.threads, k.smem) != cudaSuccess || per < 1) per = 1;
+    return (int64_t)sms * per;
+}
 
 void mdfft::detail::retile_pass(const mdfft_plan_s *p, int s, int lines, PassArgs *out, int64_t *ctas) {
     const Pass &ps = p->pass[s];
@@ -238,6 +248,9 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
         return fail(MDFFT_E_ARG, "in == out needs a plan made with MDFFT_PLAN_INPLACE");
     if (!inplace && overlaps(in, out, bytes)) return fail(MDFFT_E_ARG, "in and out overlap partially");
     if (counts && ((uintptr_t)counts % 8)) return fail(MDFFT_E_ARG, "misaligned counts pointer");
+    for (int s = 0; s < p->M; ++s)  // persistent pipelined passes copy whole 16-byte units
+        if (p->pass[s].k.persistent && (((uintptr_t)in % 16) || ((uintptr_t)out % 16)))
+            return fail(MDFFT_E_ARG, "tuned pass kernels read whole 16-byte units: align in and out to 16 bytes");
 
     const int M = p->M;
     // destination of every pass: the last one is `out`; going backwards the
@@ -260,6 +273,8 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
         a.in = src;
         a.out = dst[s];
         a.tw = (const char *)p->tw + ps.tw_offset;
+        a.ntiles = ps.ctas;
+        a.err = p->err;
         a.conj = dir == 1;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)p->T : 1.0;
         if (counts) {
@@ -268,7 +283,7 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
         }
         if (p->timing) cudaEventRecord(p->ev[slot * (M + 1) + s], st);
         void *args[] = {&a};
-        cudaError_t e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)ps.ctas), dim3(ps.k.threads), args, ps.k.smem, st);
+        cudaError_t e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)ps.grid), dim3(ps.k.threads), args, ps.k.smem, st);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
         src = dst[s];
     }
@@ -303,7 +318,8 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
     if (!out || !N) return fail(MDFFT_E_ARG, "null argument");
     *out = nullptr;
     if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
-    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE)) return fail(MDFFT_E_ARG, "unknown flag");
+    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT))
+        return fail(MDFFT_E_ARG, "unknown flag");
     if (dt != MDFFT_C64 && dt != MDFFT_C128 && dt != MDFFT_C64_TC_FP16 && dt != MDFFT_C64_TC_BF16)
         return fail(MDFFT_E_ARG, "unknown dtype");
     mdfft_plan_s *p = new (std::nothrow) mdfft_plan_s;
@@ -347,15 +363,24 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
         // every axis is transformed once: its line length must be built
         for (int i = 0; i < M; ++i) {
             PassKernel k;
-            if (!lookup(dt, p->N[i], &k)) {
+            const int64_t n = p->N[i];
+            if (!lookup(dt, n, &k)) {
                 release(p);
-                return fail(MDFFT_E_UNSUPPORTED, "line length " + std::to_string(p->N[i]) + " is not built");
+                return fail(MDFFT_E_UNSUPPORTED, "line length " + std::to_string(n) + " is not built");
             }
         }
         for (int s = 0; s < M; ++s)
             if ((st = build_pass(p, s)) != MDFFT_OK) {
                 release(p);
                 return st;
+            }
+        if ((flags & MDFFT_PLAN_PERSISTENT) && dt == MDFFT_C64)
+            for (int s = 0; s < M; ++s) {  // same tile shape: the pipelined kernel has the default's lines
+                PassKernel k;
+                if (mdfft::find_pass_kernel_pipe(p->pass[s].n, 1, &k) && k.lines == p->pass[s].k.lines) {
+                    p->pass[s].k = k;
+                    p->pass[s].grid = std::min<int64_t>(p->pass[s].ctas, mdfft::detail::wave_ctas(k));
+                }
             }
         // twiddle tables: one per pass, 256-byte aligned inside one allocation
         size_t off = 0;
@@ -365,11 +390,13 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
             off += (entries * p->elem + 255) / 256 * 256;
         }
         p->tw_bytes = off;
-        cudaError_t e = cudaMalloc(&p->tw, off);
+        cudaError_t e = cudaMalloc(&p->tw, off + 256);  // + the device error flag
         if (e != cudaSuccess) {
             release(p);
             return cuda_fail(e, "cudaMalloc twiddles");
         }
+        p->err = reinterpret_cast<int *>((char *)p->tw + off);
+        cudaMemset(p->err, 0, sizeof(int));
         for (int s = 0; s < M; ++s) {
             const int64_t n = p->pass[s].n;
             const int entries = std::max(1, mdfft::tw_entries(p->pass[s].k.plan));
@@ -565,9 +592,14 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
         Pass &ps = p->pass[s];
         std::vector<PassKernel> variants{ps.k};
         PassKernel k;
-        if (p->dt == MDFFT_C64)
+        if (p->dt == MDFFT_C64) {
             for (int thr : {256, 512})
                 if (mdfft::find_pass_kernel_c64_thr(ps.n, thr, &k) && k.threads != ps.k.threads) variants.push_back(k);
+            for (int nbuf : {1, 2})
+                if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && (uintptr_t)in % 16 == 0 &&
+                    (uintptr_t)out % 16 == 0)
+                    variants.push_back(k);
+        }
         float best_ms = -1.f, default_ms = -1.f;
         Pass best = ps;
         for (size_t v = 0; v < variants.size() && result == MDFFT_OK; ++v) {
@@ -597,17 +629,20 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 a.hblocks = (a.Nh + a.Bh - 1) / a.Bh;
                 cand.ctas = a.gblocks * a.hblocks;
                 for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
+                cand.grid = kv.persistent ? std::min<int64_t>(cand.ctas, mdfft::detail::wave_ctas(kv)) : cand.ctas;
                 a.in = in;
                 a.out = out;
                 a.tw = (const char *)p->tw + ps.tw_offset;
                 a.scale = 1.0;
+                a.ntiles = cand.ctas;
+                a.err = p->err;
                 void *args[] = {&a};
                 cudaError_t e = cudaSuccess;
                 for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.ctas), dim3(kv.threads), args, kv.smem, st);
+                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.grid), dim3(kv.threads), args, kv.smem, st);
                 cudaEventRecord(e0, st);
                 for (int r = 0; r < reps && e == cudaSuccess; ++r)
-                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.ctas), dim3(kv.threads), args, kv.smem, st);
+                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.grid), dim3(kv.threads), args, kv.smem, st);
                 cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) {
@@ -622,7 +657,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
             }
         }
         if (result != MDFFT_OK) break;
-        best.args.in = nullptr, best.args.out = nullptr, best.args.tw = nullptr;
+        best.args.in = nullptr, best.args.out = nullptr, best.args.tw = nullptr, best.args.err = nullptr;
         ps = best;
         if (ms_before) ms_before[s] = default_ms;
         if (ms_after) ms_after[s] = best_ms;
@@ -645,6 +680,21 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {
     out->ctas = ps.ctas;
     out->fft_axis = ps.f;
     out->store_axis = ps.g;
+    out->grid = ps.grid;
+    out->persistent = ps.k.persistent;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_plan_check(mdfft_plan_t p) {
+    if (!p) return fail(MDFFT_E_ARG, "null plan");
+    if (!p->err) return MDFFT_OK;
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+    if (flag) {
+        cudaMemset(p->err, 0, sizeof(int));
+        return fail(MDFFT_E_TIMEOUT, "a pass kernel's bounded wait gave up; its output is incomplete");
+    }
     return MDFFT_OK;
 }
 

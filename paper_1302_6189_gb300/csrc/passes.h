@@ -18,6 +18,10 @@
     X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(240) X(256) X(320) X(384) X(480) X(512) X(640) \
         X(768) X(960) X(1024)
 
+// Even line lengths with a persistent bulk-copy pipelined variant (two landing
+// buffers of a tile fit in shared memory).
+#define MDFFT_PIPE_LENGTHS(X) X(16) X(32) X(48) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
+
 // Line lengths with fixed-CTA-size variants for the autotuner.
 #define MDFFT_TUNED_LENGTHS(X) X(32) X(48) X(64) X(96) X(128) X(160) X(192) X(256) X(512)
 
@@ -27,12 +31,14 @@ struct PassKernel {
     const void *fn;  // __global__ fft_pass_kernel<Real, N>
     int threads, lines, tl;
     size_t smem;
-    RadixPlan plan;  // radix plan of the kernel; its twiddle table follows tw_offset()
+    RadixPlan plan;      // radix plan of the kernel; its twiddle table follows tw_offset()
+    int persistent = 0;  // > 0: walks tiles with a grid stride (launch at most one wave); landing buffers
 };
 
 bool find_pass_kernel_c64(int64_t n, PassKernel *k);
 bool find_pass_kernel_c128(int64_t n, PassKernel *k);
 bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k);  // tc: kTcFp16 or kTcBf16
 bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k);  // thr: 256 or 512 threads
+bool find_pass_kernel_pipe(int64_t n, int nbuf, PassKernel *k);    // persistent, bulk-copy pipelined
 
 }  // namespace mdfft

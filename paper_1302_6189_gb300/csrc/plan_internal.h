@@ -19,9 +19,13 @@ struct Pass {
     int64_t n = 0;             // line length N_f
     PassKernel k{};
     PassArgs args{};           // everything but in/out/tw/conj/scale/count pointers
-    int64_t ctas = 0;
+    int64_t ctas = 0;          // tiles
+    int64_t grid = 0;          // CTAs launched (= ctas, or one wave for persistent kernels)
     size_t tw_offset = 0;      // byte offset of this pass's twiddle table
 };
+
+// CTAs of one wave of kernel k on the current device (at least 1).
+int64_t wave_ctas(const PassKernel &k);
 
 // Records the message for mdfft_last_error() on this thread; returns st.
 mdfft_status fail(mdfft_status st, const std::string &msg);
@@ -55,6 +59,7 @@ struct mdfft_plan_s {
     std::vector<mdfft::planner::Layout> order;
     mdfft::detail::Pass pass[MDFFT_MAX_DIMS];
     void *tw = nullptr, *ws = nullptr, *ws2 = nullptr;
+    int *err = nullptr;           // device flag set by a persistent kernel whose bounded wait gave up
     bool external_ws = false;     // made by plan_create(..., with_workspace = false)
     size_t tw_bytes = 0;
     bool timing = false;

@@ -22,7 +22,7 @@ MAX_DIMS = 8
 MDFFT_OK, MDFFT_E_ARG, MDFFT_E_ORDER, MDFFT_E_RANGE = 0, -1, -2, -3
 MDFFT_E_NOMEM, MDFFT_E_CUDA, MDFFT_E_TIMEOUT, MDFFT_E_UNSUPPORTED = -4, -5, -6, -7
 MDFFT_C64, MDFFT_C128, MDFFT_C64_TC_FP16, MDFFT_C64_TC_BF16 = 0, 1, 2, 3
-MDFFT_PLAN_HOST_ONLY, MDFFT_PLAN_INPLACE = 0x1, 0x2
+MDFFT_PLAN_HOST_ONLY, MDFFT_PLAN_INPLACE, MDFFT_PLAN_PERSISTENT = 0x1, 0x2, 0x4
 DTYPES = {"c64": MDFFT_C64, "c128": MDFFT_C128, "c64_tc_fp16": MDFFT_C64_TC_FP16,
           "c64_tc_bf16": MDFFT_C64_TC_BF16}
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_ORDER", -3: "E_RANGE", -4: "E_NOMEM", -5: "E_CUDA",
@@ -41,7 +41,8 @@ class MdfftComm(ctypes.Structure):
 
 class MdfftPassInfo(ctypes.Structure):
     _fields_ = [("line_length", i64), ("tile_g", c_int), ("tile_h", c_int), ("threads", c_int),
-                ("smem_bytes", c_int), ("ctas", i64), ("fft_axis", c_int), ("store_axis", c_int)]
+                ("smem_bytes", c_int), ("ctas", i64), ("fft_axis", c_int), ("store_axis", c_int),
+                ("grid", i64), ("persistent", c_int)]
 
 
 class MdfftServerStats(ctypes.Structure):
@@ -65,6 +66,7 @@ SIGNATURES = {
     "mdfft_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, P_(ctypes.c_float),
                                     P_(ctypes.c_float)]),
     "mdfft_workspace_size": (c_int, [c_void_p, P_(c_size_t)]),
+    "mdfft_plan_check": (c_int, [c_void_p]),
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_supported_length": (c_int, [i64, c_int]),
     "mdfft_destroy": (c_int, [c_void_p]),
@@ -215,6 +217,10 @@ def mdfft_plan_autotune(plan, in_ptr, out_ptr, reps, stream, M):
     _check(_lib.mdfft_plan_autotune(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(reps), c_void_p(stream),
                                     before, after), "mdfft_plan_autotune")
     return list(before), list(after)
+
+
+def mdfft_plan_check(plan):
+    _check(_lib.mdfft_plan_check(plan), "mdfft_plan_check")
 
 
 def mdfft_workspace_size(plan):
@@ -400,6 +406,10 @@ class Plan:
         self._check_tensor(x, "input")
         self._check_tensor(scratch, "scratch")
         return mdfft_plan_autotune(self.handle, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream), self.M)
+
+    def check(self):
+        """Raises MdfftError (E_TIMEOUT) if a device-side bounded wait gave up."""
+        mdfft_plan_check(self.handle)
 
     def workspace_bytes(self):
         return mdfft_workspace_size(self.handle)
