@@ -278,7 +278,10 @@ def run_ours(args):
     ys = [torch.empty_like(xs[0]) for _ in range(B)]
     zs = [torch.empty_like(xs[0]) for _ in range(B)]
     stream = torch.cuda.current_stream(dev)
+    nvtx = torch.cuda.nvtx
+    nvtx.range_push("autotune")
     tune_before, tune_after = plan.autotune(xs[0], ys[0], reps=20)
+    nvtx.range_pop()
     tuned = [{k: d[k] for k in ("threads", "tile_g", "tile_h", "ctas")} for d in plan.describe()]
 
     def step():
@@ -286,9 +289,11 @@ def run_ours(args):
             plan.exec(xs[i], ys[i], dir=-1)
             plan.exec(ys[i], zs[i], dir=+1, normalize=True)
 
+    nvtx.range_push("warmup")
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
+    nvtx.range_pop()
     err = float((torch.linalg.vector_norm(zs[0] - xs[0]) / torch.linalg.vector_norm(xs[0])).item())
 
     clocks = ClockSampler(local)
@@ -298,10 +303,12 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    nvtx.range_push("timed")
     t0.record(stream)
     for _ in range(args.steps):
         step()
     t1.record(stream)
+    nvtx.range_pop()
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
@@ -317,6 +324,10 @@ def run_ours(args):
     avg_launch_ms = sum(pass_ms) / len(pass_ms)
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
     traffic = profile_traffic()
+    # the bound the redistribution's access pattern puts on a pass: the same
+    # loads and transposed stores without the butterflies
+    pattern_ms = [plan.pattern_probe(s_, xs[0], ys[0], reps=20) for s_ in range(3)]
+    pattern_gbs = launch_bytes / (sum(pattern_ms) / len(pattern_ms) * 1e-3) / 1e9
 
     # end to end: host (pinned) buffers through mdfft_exec_host, copies inside the timed region
     hx = [xs[i].cpu().pin_memory() for i in range(B)]
@@ -371,6 +382,7 @@ def run_ours(args):
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
                      "avg_launch_ms": round(avg_launch_ms, 5), "launches_timed": n_timed * 3,
+                     "pattern_bound_gbs": round(pattern_gbs, 1), "frac_of_pattern": round(achieved / pattern_gbs, 4),
                      "pass_ms": [round(v, 5) for v in pass_ms]},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * B * T * elem,

@@ -219,6 +219,19 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
 mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *out_dev, int reps, mdfft_stream_t stream,
                                  float *ms_before, float *ms_after);
 
+/*
+ * mdfft_pattern_probe -- runs `reps` times, on `stream`, a kernel that moves
+ * the data of pass s exactly like the plan's default pass kernel (same tiles,
+ * same loads, the same transposed stores into the next layout) but does no
+ * butterflies, and returns its mean duration in ms.  Its bandwidth is the
+ * bound the redistribution's access pattern puts on the pass.  complex64
+ * plans and line lengths 32, 48, 64, 96, 128, 160, 192, 256, 512 only
+ * (E_UNSUPPORTED otherwise).  in_dev is read, out_dev overwritten (T
+ * elements each); synchronises the stream.
+ */
+mdfft_status mdfft_pattern_probe(mdfft_plan_t plan, int s, const void *in_dev, void *out_dev, int reps,
+                                 mdfft_stream_t stream, float *ms);
+
 /* Waits for the device and reports whether a pass kernel of this plan gave up
  * a bounded wait since the last check (MDFFT_E_TIMEOUT; the affected output
  * is incomplete).  Only the persistent pipelined kernels that

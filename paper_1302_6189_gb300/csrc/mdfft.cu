@@ -685,6 +685,42 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {
     return MDFFT_OK;
 }
 
+mdfft_status mdfft_pattern_probe(mdfft_plan_t p, int s, const void *in, void *out, int reps, mdfft_stream_t stream,
+                                 float *ms) {
+    if (!p || !in || !out || !ms) return fail(MDFFT_E_ARG, "null argument");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan");
+    if (s < 0 || s >= p->M || reps < 1) return fail(MDFFT_E_ARG, "bad pass index or reps");
+    if (p->dt != MDFFT_C64) return fail(MDFFT_E_UNSUPPORTED, "complex64 plans only");
+    const Pass &ps = p->pass[s];
+    PassKernel k;
+    if (!mdfft::find_move_kernel_c64(ps.n, &k)) return fail(MDFFT_E_UNSUPPORTED, "no probe for this line length");
+    PassArgs a;  // the default tiling of this length
+    int64_t ctas = 0;
+    mdfft::detail::retile_pass(p, s, k.lines, &a, &ctas);
+    a.in = in, a.out = out, a.scale = 1.0, a.conj = 0, a.moved = nullptr, a.split = nullptr;
+    if (k.smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
+        return fail(MDFFT_E_CUDA, "cudaFuncSetAttribute");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchKernel(k.fn, dim3((unsigned)ctas), dim3(k.threads), args, k.smem, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = cudaLaunchKernel(k.fn, dim3((unsigned)ctas), dim3(k.threads), args, k.smem, st);
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+    *ms = t / (float)reps;
+    return MDFFT_OK;
+}
+
 mdfft_status mdfft_plan_check(mdfft_plan_t p) {
     if (!p) return fail(MDFFT_E_ARG, "null plan");
     if (!p->err) return MDFFT_OK;

@@ -40,5 +40,6 @@ bool find_pass_kernel_c128(int64_t n, PassKernel *k);
 bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k);  // tc: kTcFp16 or kTcBf16
 bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k);  // thr: 256 or 512 threads
 bool find_pass_kernel_pipe(int64_t n, int nbuf, PassKernel *k);    // persistent, bulk-copy pipelined
+bool find_move_kernel_c64(int64_t n, PassKernel *k);               // data movement of a pass, no FFT
 
 }  // namespace mdfft

@@ -67,6 +67,7 @@ SIGNATURES = {
                                     P_(ctypes.c_float)]),
     "mdfft_workspace_size": (c_int, [c_void_p, P_(c_size_t)]),
     "mdfft_plan_check": (c_int, [c_void_p]),
+    "mdfft_pattern_probe": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, P_(ctypes.c_float)]),
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_supported_length": (c_int, [i64, c_int]),
     "mdfft_destroy": (c_int, [c_void_p]),
@@ -217,6 +218,13 @@ def mdfft_plan_autotune(plan, in_ptr, out_ptr, reps, stream, M):
     _check(_lib.mdfft_plan_autotune(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(reps), c_void_p(stream),
                                     before, after), "mdfft_plan_autotune")
     return list(before), list(after)
+
+
+def mdfft_pattern_probe(plan, s, in_ptr, out_ptr, reps, stream):
+    ms = ctypes.c_float()
+    _check(_lib.mdfft_pattern_probe(plan, int(s), c_void_p(in_ptr), c_void_p(out_ptr), int(reps), c_void_p(stream),
+                                    ctypes.byref(ms)), "mdfft_pattern_probe")
+    return ms.value
 
 
 def mdfft_plan_check(plan):
@@ -406,6 +414,12 @@ class Plan:
         self._check_tensor(x, "input")
         self._check_tensor(scratch, "scratch")
         return mdfft_plan_autotune(self.handle, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream), self.M)
+
+    def pattern_probe(self, s, x, scratch, reps=10, stream=None):
+        """ms per launch of a kernel that moves pass s's data like the pass, without the FFT."""
+        self._check_tensor(x, "input")
+        self._check_tensor(scratch, "scratch")
+        return mdfft_pattern_probe(self.handle, s, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream))
 
     def check(self):
         """Raises MdfftError (E_TIMEOUT) if a device-side bounded wait gave up."""

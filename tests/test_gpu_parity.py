@@ -286,3 +286,17 @@ def test_autotune_keeps_results_bit_identical():
             assert torch.equal(before, after), shape
             for d in plan.describe():
                 assert d["tile_g"] * d["tile_h"] * (d["threads"] // max(1, d["threads"])) >= 1
+
+
+def test_pattern_probe_moves_the_data_of_a_pass():
+    # the probe kernel writes the input, untransformed, into the next layout
+    shape = (64, 48, 32)
+    x = torch.from_numpy(si.uniform_complex(shape, 97, np.complex64)).to(DEV)
+    out = torch.empty_like(x)
+    with md.Plan(shape, 4, "abc->acb->bca", "c64") as plan:
+        ms = plan.pattern_probe(0, x, out, reps=2)
+        torch.cuda.synchronize()
+    assert ms > 0
+    # pass 0 goes from layout abc to acb: element (a, b, c) lands at (a, c, b)
+    got = out.cpu().numpy().reshape(64, 32, 48)
+    assert np.array_equal(got, np.transpose(x.cpu().numpy(), (0, 2, 1)))
