@@ -81,7 +81,9 @@ typedef enum {
  *          for) unless MDFFT_PLAN_HOST_ONLY is set (then any dim >= 1).
  *   P      number of virtual processes, 1 <= P <= N_1 ... N_M (f_MD, Sec. 3.2).
  *   order  M*M axis ids as described above, or NULL for the order with the
- *          smallest total communication amount (mdfft_order_search).
+ *          smallest total communication amount (mdfft_order_search, M <= 5)
+ *          or the balanced-split heuristic's order (mdfft_order_heuristic,
+ *          M >= 6).
  *   dt     an mdfft_dtype.
  *   flags  MDFFT_PLAN_* bits.
  * Twiddles are made on the device in FP64 (sincospi) and rounded to the

@@ -353,7 +353,9 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
     } else {
         int64_t total;
         std::string err;
-        if (!pl::search_order(M, p->N, P, false, p->order, total, err)) {
+        const bool ok = M <= 5 ? pl::search_order(M, p->N, P, false, p->order, total, err)
+                               : pl::heuristic_order(M, p->N, P, p->order, total, err);
+        if (!ok) {
             release(p);
             return fail(MDFFT_E_UNSUPPORTED, "order search: " + err);
         }
@@ -519,6 +521,23 @@ mdfft_status mdfft_order_search(int M, const int64_t N[], int64_t P, int want_wo
     std::vector<pl::Layout> order;
     std::string err;
     if (!pl::search_order(M, N, P, want_worst != 0, order, *total, err)) return fail(MDFFT_E_ARG, err);
+    for (int s = 0; s < M; ++s)
+        for (int i = 0; i < M; ++i) order_out[s * M + i] = order[s].axis[i];
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_order_heuristic(int M, const int64_t N[], int64_t P, int *order_out, int64_t *total) {
+    if (!N || !order_out || !total) return fail(MDFFT_E_ARG, "null argument");
+    std::vector<pl::Layout> order;
+    std::string err;
+    if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
+    int64_t T = 1;
+    for (int i = 0; i < M; ++i) {
+        if (N[i] < 1) return fail(MDFFT_E_ARG, "dims must be >= 1");
+        T *= N[i];
+    }
+    if (P < 1 || P > T) return fail(MDFFT_E_RANGE, "P must be in [1, N_1 ... N_M]");
+    if (!pl::heuristic_order(M, N, P, order, *total, err)) return fail(MDFFT_E_ARG, err);
     for (int s = 0; s < M; ++s)
         for (int i = 0; i < M; ++i) order_out[s * M + i] = order[s].axis[i];
     return MDFFT_OK;

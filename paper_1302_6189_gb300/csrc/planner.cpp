@@ -256,5 +256,95 @@ bool search_order(int M, const int64_t *N, int64_t P, bool want_worst, std::vect
     return true;
 }
 
+// ---------------------------------------------------------------- heuristic
+
+namespace {
+
+// permutations of v in lexicographic order
+std::vector<std::vector<int>> perms_of(std::vector<int> v) {
+    std::sort(v.begin(), v.end());
+    std::vector<std::vector<int>> out;
+    do out.push_back(v);
+    while (std::next_permutation(v.begin(), v.end()));
+    return out;
+}
+
+Layout cat(int M, const std::vector<int> &front, const std::vector<int> &back) {
+    Layout L;
+    L.M = M;
+    int i = 0;
+    for (int a : front) L.axis[i++] = a;
+    for (int a : back) L.axis[i++] = a;
+    return L;
+}
+
+bool lex_less(const Layout &a, const Layout &b) {
+    for (int i = 0; i < a.M; ++i)
+        if (a.axis[i] != b.axis[i]) return a.axis[i] < b.axis[i];
+    return false;
+}
+
+int64_t split_order(int M, const int64_t *N, int64_t P, int p, std::vector<Layout> &order) {
+    std::vector<int> X, Y;
+    for (int i = 0; i < M; ++i) (i < p ? X : Y).push_back(i);
+    const auto px = perms_of(X), py = perms_of(Y);
+    order.clear();
+    order.push_back(cat(M, X, Y));
+    unsigned used = 1u << (M - 1);
+    int64_t total = 0;
+    auto pick = [&](const std::vector<Layout> &family) {
+        const Layout &cur = order.back();
+        bool have = false;
+        int64_t best = 0;
+        Layout bestL;
+        for (const Layout &L : family) {
+            const int last = L.axis[M - 1];
+            if (used & (1u << last)) continue;
+            const int64_t v = transition_amount(M, N, P, cur, L);
+            if (!have || v < best || (v == best && lex_less(L, bestL))) have = true, best = v, bestL = L;
+        }
+        order.push_back(bestL);
+        used |= 1u << bestL.axis[M - 1];
+        total += best;
+    };
+    std::vector<Layout> fam1, fam2;
+    for (const auto &y : py) fam1.push_back(cat(M, X, y));
+    for (const auto &y : py)
+        for (const auto &x : px) fam2.push_back(cat(M, y, x));
+    for (size_t k = 1; k < Y.size(); ++k) pick(fam1);  // the rest of Y, X in front
+    for (size_t k = 0; k < X.size(); ++k) pick(fam2);  // Y in front, the axes of X
+    return total;
+}
+
+}  // namespace
+
+bool heuristic_order(int M, const int64_t *N, int64_t P, std::vector<Layout> &order, int64_t &total,
+                     std::string &err) {
+    if (M < 2 || M > kMaxDims) {
+        err = "heuristic supports 2 <= M <= 8";
+        return false;
+    }
+    int64_t T = 1;
+    for (int i = 0; i < M; ++i) {
+        if (N[i] < 1) {
+            err = "dims must be >= 1";
+            return false;
+        }
+        T *= N[i];
+    }
+    if (P < 1 || P > T) {
+        err = "P out of range";
+        return false;
+    }
+    bool have = false;
+    for (int p : {M / 2, (M + 1) / 2}) {
+        if (p < 1 || p >= M) continue;
+        std::vector<Layout> o;
+        const int64_t t = split_order(M, N, P, p, o);
+        if (!have || t < total) order = o, total = t, have = true;
+    }
+    return have;
+}
+
 }  // namespace planner
 }  // namespace mdfft

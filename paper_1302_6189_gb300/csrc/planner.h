@@ -60,5 +60,15 @@ std::string check_order(int M, const std::vector<Layout> &order);
 bool search_order(int M, const int64_t *N, int64_t P, bool want_worst, std::vector<Layout> &order,
                   int64_t &total, std::string &err);
 
+// Balanced-split heuristic for any M >= 2 (the form the paper suggests for
+// higher dimensions, Sec. 3.3): axes split X | Y; first every axis of Y is
+// transformed with X in front (layouts X . perm(Y)), then a permutation of Y
+// moves to the front and the axes of X are transformed (layouts perm(Y) .
+// perm(X)).  Each next layout is the one of that family with the smallest
+// amount from the current layout (ties: lexicographically smallest); both
+// splits |X| = floor(M/2) and ceil(M/2) are tried and the smaller total kept.
+bool heuristic_order(int M, const int64_t *N, int64_t P, std::vector<Layout> &order, int64_t &total,
+                     std::string &err);
+
 }  // namespace planner
 }  // namespace mdfft

@@ -59,6 +59,7 @@ SIGNATURES = {
     "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
     "mdfft_plan_order": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_order_search": (c_int, [c_int, P_(i64), i64, c_int, P_(c_int), P_(i64)]),
+    "mdfft_order_heuristic": (c_int, [c_int, P_(i64), i64, P_(c_int), P_(i64)]),
     "mdfft_pass_timing": (c_int, [c_void_p, c_int]),
     "mdfft_pass_times": (c_int, [c_void_p, P_(ctypes.c_float), c_int, P_(c_int)]),
     "mdfft_exec_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -186,6 +187,14 @@ def mdfft_order_search(N, P, want_worst=0):
     tot = i64()
     _check(_lib.mdfft_order_search(M, dims, int(P), int(want_worst), arr, ctypes.byref(tot)),
            "mdfft_order_search")
+    return [list(arr[s * M:(s + 1) * M]) for s in range(M)], tot.value
+
+
+def mdfft_order_heuristic(N, P):
+    dims, M = _dims(N)
+    arr = (c_int * (M * M))()
+    tot = i64()
+    _check(_lib.mdfft_order_heuristic(M, dims, int(P), arr, ctypes.byref(tot)), "mdfft_order_heuristic")
     return [list(arr[s * M:(s + 1) * M]) for s in range(M)], tot.value
 
 

@@ -300,3 +300,13 @@ def test_pattern_probe_moves_the_data_of_a_pass():
     # pass 0 goes from layout abc to acb: element (a, b, c) lands at (a, c, b)
     got = out.cpu().numpy().reshape(64, 32, 48)
     assert np.array_equal(got, np.transpose(x.cpu().numpy(), (0, 2, 1)))
+
+
+@pytest.mark.parametrize("shape", [(4, 2, 3, 2, 4, 2), (2, 2, 3, 2, 2, 2, 5), (2, 3, 2, 2, 2, 2, 2, 4)])
+def test_six_to_eight_dims_with_the_heuristic_order(shape):
+    x = si.uniform_complex(shape, 98)
+    for dt in ("c64", "c128"):
+        y, _ = run(shape, 5, None, dt, x)
+        check(y, oracle.fftn(x), dt, str(shape))
+        yi, _ = run(shape, 5, None, dt, x, dir=+1, normalize=True)
+        check(yi * 1.0, oracle.fftn(x, sign=+1) / x.size, dt, "inverse " + str(shape))

@@ -153,3 +153,38 @@ def test_supported_lengths():
         assert md.mdfft_supported_length(n, "c64") and md.mdfft_supported_length(n, "c128")
     for n in (7, 11, 2048, 0, -4):
         assert not md.mdfft_supported_length(n, "c64")
+
+
+@pytest.mark.parametrize("N,Ps", [((8, 8, 8, 8), (2, 16, 64, 100, 512)), ((4, 4, 4, 4, 4), (2, 16, 64, 200)),
+                                  ((3, 4, 2, 3), (5, 12, 30)), ((6, 4, 5), (3, 12, 40))])
+def test_balanced_split_heuristic_against_exhaustive(N, Ps):
+    # Sec. 3.3's balanced two-part form: equal to the exhaustive optimum in
+    # the low regimes for cubes, never below it, always a valid order
+    for P in Ps:
+        order, total = md.mdfft_order_heuristic(N, P)
+        ref = oracle.order_search(N, P, best_cap=1)
+        assert total >= ref["best"]
+        assert oracle.comm_volume(N, P, order)["total"] == total
+        M = len(N)
+        assert order[0] == list(range(M)) and sorted(L[-1] for L in order) == list(range(M))
+        if len(set(N)) == 1 and P <= N[0] ** (M // 2) and N[0] ** (M // 2) % P == 0:
+            assert total == ref["best"]
+
+
+def test_heuristic_for_six_to_eight_dims():
+    # (M-1)!^M orders are too many from M = 6 on (Table 1); in the low regime
+    # of a cube the heuristic reaches the closed-form optimum T (1 - 1/P)
+    for M, n, Ps in [(6, 4, (2, 4, 16, 64)), (7, 2, (2, 4, 8)), (8, 2, (2, 4, 16))]:
+        N = (n,) * M
+        T = n ** M
+        for P in Ps:
+            order, total = md.mdfft_order_heuristic(N, P)
+            assert total * P == T * (P - 1)
+            assert oracle.comm_volume(N, P, order)["total"] == total
+    # without an order, plans of 6-8 dims use it
+    for N in [(4, 2, 3, 2, 4, 2), (2, 2, 3, 2, 2, 2, 2), (2,) * 8]:
+        h = md.mdfft_plan(N, 4, None, "c64", HOST)
+        try:
+            assert md.mdfft_plan_order(h, len(N)) == md.mdfft_order_heuristic(N, 4)[0]
+        finally:
+            md.mdfft_destroy(h)
