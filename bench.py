@@ -181,11 +181,13 @@ def barrier(world):
 
 
 def max_over_ranks(value, world):
+    """Max of a per-rank time over all ranks (NCCL: on the device; gloo: on the host)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -152,6 +152,18 @@ mdfft_status mdfft_comm_volume(mdfft_plan_t plan, mdfft_comm *out);
 mdfft_status mdfft_chunk(mdfft_plan_t plan, int step, int64_t pid, int64_t *xs, int64_t *xe,
                          int64_t start_coord[], int64_t end_coord[]);
 
+/*
+ * mdfft_exchange_counts -- the all-to-all-v of transition `step` (layout step
+ * to step+1; step = M-1: the last layout back to natural order) when the P
+ * virtual processes are laid onto G devices in contiguous blocks (device g
+ * holds processes floor(gP/G) .. floor((g+1)P/G)-1, i.e. one contiguous
+ * row-major range of every layout).  counts (G*G int64): [g*G + h] = points
+ * device g holds before the transition and device h after it; the
+ * off-diagonal sum is the data that crosses devices (at most the plan's
+ * per-transition amount).  Host only; 1 <= G <= P.
+ */
+mdfft_status mdfft_exchange_counts(mdfft_plan_t plan, int step, int G, int64_t *counts);
+
 /* The plan's order (M*M ints), e.g. the one the planner picked for order = NULL. */
 mdfft_status mdfft_plan_order(mdfft_plan_t plan, int *order_out);
 

@@ -502,6 +502,19 @@ mdfft_status mdfft_chunk(mdfft_plan_t p, int step, int64_t pid, int64_t *xs, int
     return MDFFT_OK;
 }
 
+mdfft_status mdfft_exchange_counts(mdfft_plan_t p, int step, int G, int64_t *counts) {
+    if (!p || !counts) return fail(MDFFT_E_ARG, "null argument");
+    if (step < 0 || step >= p->M) return fail(MDFFT_E_ARG, "step out of range");
+    if (G < 1 || G > p->P) return fail(MDFFT_E_ARG, "G must be in [1, P]");
+    pl::Layout nat;
+    nat.M = p->M;
+    for (int i = 0; i < p->M; ++i) nat.axis[i] = i;
+    const pl::Layout &A = p->order[step];
+    const pl::Layout &B = step + 1 < p->M ? p->order[step + 1] : nat;
+    pl::exchange_counts(p->M, p->N, p->P, A, B, G, counts);
+    return MDFFT_OK;
+}
+
 mdfft_status mdfft_plan_order(mdfft_plan_t p, int *order_out) {
     if (!p || !order_out) return fail(MDFFT_E_ARG, "null argument");
     for (int s = 0; s < p->M; ++s)

@@ -141,6 +141,25 @@ int64_t split_line_amount(int M, const int64_t *N, int64_t P, const Layout &L) {
     return nf * cuts;
 }
 
+void exchange_counts(int M, const int64_t *N, int64_t P, const Layout &A, const Layout &B, int G, int64_t *counts) {
+    int64_t da[kMaxDims], db[kMaxDims];
+    layout_dims(A, N, da);
+    layout_dims(B, N, db);
+    std::vector<std::vector<Box>> ba(G), bb(G);
+    for (int g = 0; g < G; ++g) {
+        const int64_t p0 = (int64_t)g * P / G, p1 = (int64_t)(g + 1) * P / G;
+        range_boxes(A, N, fmd(M, da, P, p0), fmd(M, da, P, p1), ba[g]);
+        range_boxes(B, N, fmd(M, db, P, p0), fmd(M, db, P, p1), bb[g]);
+    }
+    for (int g = 0; g < G; ++g)
+        for (int h = 0; h < G; ++h) {
+            int64_t c = 0;
+            for (const Box &x : ba[g])
+                for (const Box &y : bb[h]) c += overlap(M, x, y);
+            counts[(size_t)g * G + h] = c;
+        }
+}
+
 std::string check_order(int M, const std::vector<Layout> &order) {
     if ((int)order.size() != M) return "order must have M layouts";
     bool used_last[kMaxDims] = {false};

@@ -60,6 +60,12 @@ std::string check_order(int M, const std::vector<Layout> &order);
 bool search_order(int M, const int64_t *N, int64_t P, bool want_worst, std::vector<Layout> &order,
                   int64_t &total, std::string &err);
 
+// All-to-all-v counts of the transition A -> B when the P processes are laid
+// onto G devices in contiguous blocks (device g holds processes
+// floor(g P / G) .. floor((g+1) P / G) - 1, a contiguous row-major range):
+// counts[g * G + h] = points held by g in A and by h in B.
+void exchange_counts(int M, const int64_t *N, int64_t P, const Layout &A, const Layout &B, int G, int64_t *counts);
+
 // Balanced-split heuristic for any M >= 2 (the form the paper suggests for
 // higher dimensions, Sec. 3.3): axes split X | Y; first every axis of Y is
 // transformed with X in front (layouts X . perm(Y)), then a permutation of Y

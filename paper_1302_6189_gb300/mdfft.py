@@ -58,6 +58,7 @@ SIGNATURES = {
     "mdfft_comm_volume": (c_int, [c_void_p, P_(MdfftComm)]),
     "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
     "mdfft_plan_order": (c_int, [c_void_p, P_(c_int)]),
+    "mdfft_exchange_counts": (c_int, [c_void_p, c_int, c_int, P_(i64)]),
     "mdfft_order_search": (c_int, [c_int, P_(i64), i64, c_int, P_(c_int), P_(i64)]),
     "mdfft_order_heuristic": (c_int, [c_int, P_(i64), i64, P_(c_int), P_(i64)]),
     "mdfft_pass_timing": (c_int, [c_void_p, c_int]),
@@ -173,6 +174,12 @@ def mdfft_chunk(plan, step, pid, M):
     _check(_lib.mdfft_chunk(plan, int(step), int(pid), ctypes.byref(xs), ctypes.byref(xe), cs, ce),
            "mdfft_chunk")
     return xs.value, xe.value, list(cs), list(ce)
+
+
+def mdfft_exchange_counts(plan, step, G):
+    arr = (i64 * (G * G))()
+    _check(_lib.mdfft_exchange_counts(plan, int(step), int(G), arr), "mdfft_exchange_counts")
+    return [list(arr[g * G:(g + 1) * G]) for g in range(G)]
 
 
 def mdfft_plan_order(plan, M):
