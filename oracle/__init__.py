@@ -90,6 +90,7 @@ def _load():
             "orc_amount_slab": (dbl, [dbl, dbl]),
             "orc_amount_pencil": (dbl, [dbl, dbl]),
             "orc_amount_volumetric": (dbl, [c_int, dbl, dbl]),
+            "orc_block_volume": (c_int, [c_int, P(i64), i64, c_int, P(c_int), P(i64), P(i64), P(i64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -324,3 +325,25 @@ def amount_pencil(N, P):
 
 def amount_volumetric(M, N, P):
     return _load().orc_amount_volumetric(int(M), float(N), float(P))
+
+
+BLOCK_KINDS = {"slab": 1, "pencil": 2, "volumetric": 3}
+
+
+def block_volume(N, P, kind, fft_axes):
+    """Amounts of a comparison method of Sec. 4 (kind 'slab', 'pencil' or
+    'volumetric') whose steps transform fft_axes in turn, counted point by
+    point; q[s][axis] = processes along that axis in step s."""
+    dims, M = _dims(N)
+    per = np.zeros(max(M - 1, 1), np.int64)
+    spl = np.zeros(M, np.int64)
+    q = np.zeros((M, M), np.int64)
+    ax = (ctypes.c_int * M)(*[int(a) for a in fft_axes])
+    rc = _load().orc_block_volume(M, dims, int(P), BLOCK_KINDS[kind], ax, _ptr(per, ctypes.c_int64),
+                                  _ptr(spl, ctypes.c_int64), _ptr(q, ctypes.c_int64))
+    if rc == -2:
+        raise ValueError(f"{kind}: more blocks than points along a cut axis (P = {P})")
+    _check(rc, "block_volume")
+    per = per[: M - 1]
+    return {"per_transition": per.tolist(), "total": int(per.sum()), "split_line": spl.tolist(),
+            "paper_total": int(per.sum() + spl.sum()), "q": q.tolist()}

@@ -25,10 +25,12 @@
  *   6. enumeration of transpose orders               (Sec. 3.2, the C_MD equation; Table 1)
  *   7. the parallel algorithm of Fig. 4 with explicit per-rank chunk buffers
  *   8. closed-form amounts of the comparison methods (Sec. 4, A_1D ... A_5D)
+ *   9. the comparison methods as owners of every point (Sec. 4), brute force
  *
  * Parity status: every part is pinned by the tests against values that do
  * not come from this file (naive DFT, numpy.fft, closed-form spectra, the
- * paper's Table 1, its printed ratios and its worked 2-D-regime statement).
+ * paper's Table 1, its printed ratios and its worked 2-D-regime statement,
+ * and the closed forms A_1D ... A_5D of Sec. 4 for part 9).
  */
 #include <math.h>
 #include <pthread.h>
@@ -757,4 +759,125 @@ double orc_amount_pencil(double N, double P) { return 2.0 * N * N * N - 2.0 * P 
 double orc_amount_volumetric(int M, double N, double P) {
     double T = pow(N, (double)M);
     return (double)M * T * (N / pow(T / P, 1.0 / (double)M) - 1.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 9. The comparison methods of Sec. 4 as explicit owners of every point.    */
+/*    The 1-D method gives each process whole planes (one axis cut), the     */
+/*    2-D method whole lines (two axes cut), the M-D methods blocks (every   */
+/*    axis cut).  A step transforms along one axis.  With fewer than M cut   */
+/*    axes the transformed axis is never cut: when the next step's axis is   */
+/*    cut, its cut moves to the axis just transformed (the transposes of the */
+/*    1-D and 2-D methods).  With M cut axes nothing moves and every line is */
+/*    shared by the owners of its blocks, each of which gathers the whole    */
+/*    line (the model behind A_3D: T (q - 1) points per step).               */
+/*    Readings of what Sec. 4 leaves open:                                    */
+/*    - the cut axes of the first step are the k slowest axes a, b, ...      */
+/*      (the first step transforms the fastest axis);                         */
+/*    - Np is split over the k cuts as evenly as possible: its prime factors,*/
+/*      largest first, each go to the cut with the smallest product so far  */
+/*      (the first such cut on ties); pid = sum_j digit_j prod_{i>j} q_i;    */
+/*    - a cut of n points into q blocks gives block j the points             */
+/*      [floor(j n / q), floor((j + 1) n / q)), the floor rule of f_MD's 1-D */
+/*      case; q <= n, so no block is empty;                                   */
+/*    - the output stays in the last step's decomposition.                    */
+/* ------------------------------------------------------------------------ */
+
+static void even_split(int64_t P, int k, int64_t *q) {
+    int64_t f[64];
+    int nf = 0;
+    int64_t n = P;
+    for (int64_t d = 2; d * d <= n; ++d)
+        while (n % d == 0) f[nf++] = d, n /= d;
+    if (n > 1) f[nf++] = n;
+    for (int j = 0; j < k; ++j) q[j] = 1;
+    for (int i = nf - 1; i >= 0; --i) {
+        int jm = 0;
+        for (int j = 1; j < k; ++j)
+            if (q[j] < q[jm]) jm = j;
+        q[jm] *= f[i];
+    }
+}
+
+/* kind: 1 = 1-D (slab), 2 = 2-D (pencil), 3 = M-D (volumetric) method.
+ * fft_axes[s]: the axis transformed in step s (a permutation of 0..M-1).
+ * Writes per_transition[s] (s < M-1): points whose owner differs between
+ * steps s and s+1; split[s]: sum over the lines of step s of
+ * N_axis (owners on the line - 1); q_axis[s*M + axis]: processes along that
+ * axis in step s (1: not cut).  Every count is by looking at every point.
+ * Returns 0, -1 on bad arguments, -2 if a cut has more blocks than points,
+ * -3 on allocation failure. */
+int orc_block_volume(int M, const int64_t *N, int64_t P, int kind, const int *fft_axes, int64_t *per_transition,
+                     int64_t *split, int64_t *q_axis) {
+    if (M < 1 || M > ORC_MAXDIM || kind < 1 || kind > 3 || P < 1) return -1;
+    int used[ORC_MAXDIM] = {0};
+    for (int s = 0; s < M; ++s) {
+        if (fft_axes[s] < 0 || fft_axes[s] >= M || used[fft_axes[s]]) return -1;
+        used[fft_axes[s]] = 1;
+    }
+    const int k = kind == 3 ? M : kind;
+    if (k > M) return -1;
+    int64_t q[ORC_MAXDIM];
+    even_split(P, k, q);
+    int cut[ORC_MAXDIM][ORC_MAXDIM]; /* [step][j]: the axis of cut j */
+    for (int j = 0; j < k; ++j) cut[0][j] = j;
+    for (int s = 0; s < M; ++s) {
+        if (s > 0)
+            for (int j = 0; j < k; ++j) {
+                cut[s][j] = cut[s - 1][j];
+                if (k < M && cut[s][j] == fft_axes[s]) cut[s][j] = fft_axes[s - 1];
+            }
+        for (int a = 0; a < M; ++a) q_axis[s * M + a] = 1;
+        for (int j = 0; j < k; ++j) {
+            if (k < M && cut[s][j] == fft_axes[s]) return -1;
+            if (q[j] > N[cut[s][j]]) return -2;
+            q_axis[s * M + cut[s][j]] = q[j];
+        }
+    }
+    int64_t T = 1;
+    for (int i = 0; i < M; ++i) T *= N[i];
+    int64_t *own = (int64_t *)malloc((size_t)T * sizeof(int64_t) * 2);
+    int64_t *seen = (int64_t *)malloc((size_t)P * sizeof(int64_t));
+    if (!own || !seen) {
+        free(own), free(seen);
+        return -3;
+    }
+    int64_t c[ORC_MAXDIM];
+    for (int s = 0; s < M; ++s) {
+        int64_t *cur = own + (s % 2) * T, *prev = own + ((s + 1) % 2) * T;
+        for (int64_t X = 0; X < T; ++X) {
+            orc_coords(M, N, X, c);
+            int64_t pid = 0;
+            for (int j = 0; j < k; ++j) {
+                const int64_t n = N[cut[s][j]], x = c[cut[s][j]];
+                int64_t b = 0; /* the block of x: the largest b with floor(b n / q) <= x */
+                while (b + 1 < q[j] && ((b + 1) * n) / q[j] <= x) ++b;
+                pid = pid * q[j] + b;
+            }
+            cur[X] = pid;
+        }
+        if (s > 0) {
+            int64_t m = 0;
+            for (int64_t X = 0; X < T; ++X) m += cur[X] != prev[X];
+            per_transition[s - 1] = m;
+        }
+        /* owners on every line along the step's axis */
+        const int f = fft_axes[s];
+        int64_t stride = 1;
+        for (int i = M - 1; i > f; --i) stride *= N[i];
+        for (int64_t p = 0; p < P; ++p) seen[p] = -1;
+        split[s] = 0;
+        for (int64_t X = 0; X < T; ++X) {
+            orc_coords(M, N, X, c);
+            if (c[f] != 0) continue; /* X is the first point of its line */
+            int64_t owners = 0;
+            for (int64_t t = 0; t < N[f]; ++t) {
+                const int64_t pid = cur[X + t * stride];
+                if (seen[pid] != X) seen[pid] = X, ++owners;
+            }
+            split[s] += N[f] * (owners - 1);
+        }
+    }
+    free(own), free(seen);
+    return 0;
 }
