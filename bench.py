@@ -451,8 +451,48 @@ def extra_table(dev, x, P):
                    "nominal_tflops_fp64": round(flops / (ms * 1e-3) / 1e12, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms]}
     res["precision_512cubed"] = precision_study(dev)
+    res["decompositions"] = decomposition_study(dev)
     res["serving"] = serving_study(dev)
     return res
+
+
+def decomposition_study(dev):
+    """Amounts of communication (points) counted on the device by the pass
+    kernels for the row-wise method (best order) and the comparison methods
+    of Sec. 4 run through the same passes, beside the closed forms: 64^3 as
+    in Fig. 7, 16^4 and 16^5 as in Fig. 8."""
+    import torch
+
+    from paper_1302_6189_gb300 import DECOMPOSITIONS, MdfftError, Plan
+
+    cases = {(64, 64, 64): (4, 16, 64, 256, 1024, 4096, 8192, 32768, 262144),
+             (16, 16, 16, 16): (16, 256, 4096, 65536), (16,) * 5: (32, 1024, 4096, 32768)}
+    out = {}
+    for shape, Ps in cases.items():
+        M = len(shape)
+        x = torch.zeros(shape, dtype=torch.complex64, device=dev)
+        rows = []
+        for P in Ps:
+            row = {"P": P}
+            for kind, flag in DECOMPOSITIONS.items():
+                try:
+                    with Plan(shape, P, None, "c64", flag) as pl:
+                        _, c = pl.exec_counted(x)
+                        c = c.cpu().tolist()
+                        cv = pl.comm_volume()
+                except MdfftError:
+                    row[kind] = None  # the method cannot use P processes on this grid
+                    continue
+                row[kind] = int(sum(c[: M - 1]) + sum(c[M:]))
+                row["A_1D"] = cv["amount_slab"]
+                row["A_2D"] = cv["amount_pencil"] if M == 3 else None
+                row["A_MD"] = cv["amount_volumetric"]
+            for kind in ("slab", "pencil", "volumetric"):
+                if row.get(kind):
+                    row[f"{kind}_over_rowwise"] = round(row[kind] / row["rowwise"], 3)
+            rows.append(row)
+        out["x".join(map(str, shape))] = rows
+    return out
 
 
 def precision_study(dev):

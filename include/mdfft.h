@@ -70,6 +70,23 @@ typedef enum {
 #define MDFFT_PLAN_PERSISTENT 0x4u /* complex64: use the persistent bulk-copy pipelined pass kernel
                                       wherever one is built (even lengths <= 512); arrays must then be
                                       16-byte aligned */
+/*
+ * Ownership model of the plan's counted amounts (mdfft_comm_volume,
+ * mdfft_exec_counted).  Default: the row-wise f_MD chunks of Sec. 3.  At most
+ * one of the following selects a comparison method of Sec. 4 instead, run
+ * through the same passes and order (step s transforms the last axis of
+ * layout s): the 1-D method (whole planes: one axis cut), the 2-D method
+ * (whole lines: two axes cut, M >= 3) or the volumetric M-D method (blocks:
+ * every axis cut, each line gathered by each of its owners).  With fewer
+ * than M cut axes, the cut of the axis about to be transformed moves to the
+ * axis just transformed; the first step cuts the slowest axes; P is split
+ * over the cuts as evenly as possible (prime factors, largest first, each to
+ * the cut with the smallest product); a cut of n points into q blocks needs
+ * q <= n (else E_RANGE).  The output stays in the last step's decomposition.
+ */
+#define MDFFT_PLAN_DECOMP_SLAB 0x10u
+#define MDFFT_PLAN_DECOMP_PENCIL 0x20u
+#define MDFFT_PLAN_DECOMP_VOLUMETRIC 0x40u
 
 /*
  * mdfft_plan -- build a plan for the M-D FFT of dims N[0..M) with Np = P
@@ -126,10 +143,12 @@ mdfft_status mdfft_exec_counted(mdfft_plan_t plan, const void *in_dev, void *out
 typedef struct {
     int64_t per_transition[MDFFT_MAX_DIMS]; /* [s], s < M-1: points whose owner changes from layout s to s+1 */
     int64_t total;                          /* sum of per_transition: what the order search minimises */
-    int64_t final_to_natural;               /* last layout back to natural order (done, not counted) */
+    int64_t final_to_natural;               /* last layout back to natural order (done, not counted; 0 for
+                                               the comparison methods, whose output stays where it is) */
     int64_t split_line[MDFFT_MAX_DIMS];     /* [s]: sum over lines of layout s cut between k owners of N_axis (k-1) */
     int64_t paper_total;                    /* total + sum(split_line): comparable with the Sec. 4 closed forms */
-    int regime[MDFFT_MAX_DIMS];             /* [s]: leading dims of layout s that chunks are cut on (f_MD case) */
+    int regime[MDFFT_MAX_DIMS];             /* [s]: leading dims of layout s that chunks are cut on (f_MD case);
+                                               axes cut per step for the comparison methods */
     double amount_slab;                     /* Sec. 4 closed forms for the same T and Np: T - T/Np */
     double amount_pencil;                   /* 2N^3 - 2Np (N^2/Np)^(3/2); NaN unless M = 3 and N_1 = N_2 = N_3 */
     double amount_volumetric;               /* M N^M (N / (N^M/Np)^(1/M) - 1); NaN unless all dims equal */
@@ -138,12 +157,14 @@ typedef struct {
 /*
  * mdfft_comm_volume -- the plan's amounts, computed on the host by
  * intersecting chunk boxes (every chunk of a row-major range is a union of
- * at most 2M-1 axis-aligned boxes).  Works on MDFFT_PLAN_HOST_ONLY plans.
+ * at most 2M-1 axis-aligned boxes; a comparison method's block is one box).
+ * The ownership model is the plan's (MDFFT_PLAN_DECOMP_*).  Works on
+ * MDFFT_PLAN_HOST_ONLY plans.
  */
 mdfft_status mdfft_comm_volume(mdfft_plan_t plan, mdfft_comm *out);
 
 /*
- * mdfft_chunk -- the index map of Sec. 3.2 for process pid in layout `step`
+ * mdfft_chunk -- (row-wise plans) the index map of Sec. 3.2 for process pid in layout `step`
  * (0..M-1; M means the natural output layout): x^s = f_MD(pid),
  * x^e = f_MD(pid+1) - 1 over the dims permuted into that layout, and their
  * coordinates in the layout's axis order (start_coord/end_coord: M entries
@@ -160,9 +181,16 @@ mdfft_status mdfft_chunk(mdfft_plan_t plan, int step, int64_t pid, int64_t *xs, 
  * row-major range of every layout).  counts (G*G int64): [g*G + h] = points
  * device g holds before the transition and device h after it; the
  * off-diagonal sum is the data that crosses devices (at most the plan's
- * per-transition amount).  Host only; 1 <= G <= P.
+ * per-transition amount).  Host only; 1 <= G <= P; row-wise plans only.
  */
 mdfft_status mdfft_exchange_counts(mdfft_plan_t plan, int step, int G, int64_t *counts);
+
+/*
+ * mdfft_block_grid -- for a plan made with an MDFFT_PLAN_DECOMP_* flag: the
+ * blocks every natural axis is cut into in step `step` (0..M-1), q_axis[M]
+ * (1: not cut).  E_ARG for row-wise plans or a step out of range.
+ */
+mdfft_status mdfft_block_grid(mdfft_plan_t plan, int step, int64_t *q_axis);
 
 /* The plan's order (M*M ints), e.g. the one the planner picked for order = NULL. */
 mdfft_status mdfft_plan_order(mdfft_plan_t plan, int *order_out);

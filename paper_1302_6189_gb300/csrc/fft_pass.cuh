@@ -32,11 +32,19 @@ namespace mdfft {
 
 constexpr int kMaxTileDims = 8;
 
-// Owner of a row-major index x of a layout under f_MD chunks (Sec. 3.2):
-// with q = x / tail (the index over the `lead` product of the leading dims
-// the chunks are cut on), owner = floor(((q + 1) P - 1) / lead).
+// Owner of a row-major index x of a layout.  f_MD chunks (Sec. 3.2, blk
+// null): with q = x / tail (the index over the `lead` product of the leading
+// dims the chunks are cut on), owner = floor(((q + 1) P - 1) / lead).  Block
+// decompositions of the comparison methods (Sec. 4, blk non-null): blk holds
+// 3 nd entries, per layout position (slowest first) its extent d, the blocks
+// q it is cut into and the pid stride ps; a coordinate c lies in block
+// floor(((c + 1) q - 1) / d) and owner = sum of block * ps.  line_div turns
+// the owner difference of a line's ends into the owners on it minus one.
 struct OwnerMap {
     int64_t tail, lead, P;
+    const int64_t *blk;
+    int nd;
+    int64_t line_div;
 };
 
 struct PassArgs {
@@ -269,6 +277,16 @@ template <int G> __device__ __forceinline__ int padg(int i) { return i + i / G; 
 namespace mdfft {
 
 __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
+    if (m.blk) {
+        int64_t pid = 0;
+        for (int i = m.nd - 1; i >= 0; --i) {
+            const int64_t d = m.blk[i], q = m.blk[m.nd + i];
+            const int64_t c = x % d;
+            x /= d;
+            if (q > 1) pid += (((c + 1) * q - 1) / d) * m.blk[2 * m.nd + i];
+        }
+        return pid;
+    }
     unsigned __int128 q = (unsigned __int128)(x / m.tail);
     return (int64_t)(((q + 1) * (unsigned __int128)m.P - 1) / (unsigned __int128)m.lead);
 }
@@ -420,7 +438,9 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
             const int64_t ib = lbase[sl];
             for (int k = k0; k < N; k += Cfg::TL)
                 moved += owner_of(a.own_in, ib + k) != owner_of(a.own_out, obase + k * a.out_sf);
-            if (k0 == 0) split = (unsigned long long)N * (owner_of(a.own_in, ib + N - 1) - owner_of(a.own_in, ib));
+            if (k0 == 0)
+                split = (unsigned long long)N *
+                        ((owner_of(a.own_in, ib + N - 1) - owner_of(a.own_in, ib)) / a.own_in.line_div);
         }
     }
     if (a.moved) {

@@ -61,9 +61,43 @@ mdfft::OwnerMap owner_map(int M, const int64_t *N, int64_t P, const pl::Layout &
     int64_t d[pl::kMaxDims];
     pl::layout_dims(L, N, d);
     int k = pl::regime(M, d, P);
-    mdfft::OwnerMap m{1, 1, P};
+    mdfft::OwnerMap m{1, 1, P, nullptr, 0, 1};
     for (int i = 0; i < M; ++i) (i < k ? m.lead : m.tail) *= d[i];
     return m;
+}
+
+// Owner tables of a comparison method (OwnerMap::blk): table t < M is layout
+// t with the ownership of step t, table M the natural layout with the
+// ownership of the last step; each holds d, q, ps per layout position.
+std::vector<int64_t> owner_tables(const mdfft_plan_s *p) {
+    std::vector<int64_t> tab;
+    if (p->bd.kind == pl::kRowwise) return tab;
+    const int M = p->M;
+    tab.resize((size_t)(M + 1) * 3 * M);
+    for (int t = 0; t <= M; ++t) {
+        const int step = t < M ? t : M - 1;
+        int64_t q[pl::kMaxDims], ps[pl::kMaxDims];
+        pl::block_axis_grid(p->bd, M, step, q, ps);
+        int64_t *row = &tab[(size_t)t * 3 * M];
+        for (int i = 0; i < M; ++i) {
+            const int ax = t < M ? p->order[t].axis[i] : i;
+            row[i] = p->N[ax], row[M + i] = q[ax], row[2 * M + i] = ps[ax];
+        }
+    }
+    return tab;
+}
+
+// Points the pass kernels' count mode at the owner tables (device copy at tab).
+void set_block_owners(mdfft_plan_s *p, const int64_t *tab) {
+    const int M = p->M;
+    for (int s = 0; s < M; ++s) {
+        PassArgs &a = p->pass[s].args;
+        int64_t q[pl::kMaxDims], ps[pl::kMaxDims];
+        pl::block_axis_grid(p->bd, M, s, q, ps);
+        const int f = p->order[s].axis[M - 1];
+        a.own_in = mdfft::OwnerMap{1, 1, p->P, tab + (size_t)s * 3 * M, M, q[f] > 1 ? ps[f] : 1};
+        a.own_out = mdfft::OwnerMap{1, 1, p->P, tab + (size_t)(s + 1) * 3 * M, M, 1};
+    }
 }
 
 // Kernel for a line length: the tensor-core dtypes use the tensor-core
@@ -318,8 +352,11 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
     if (!out || !N) return fail(MDFFT_E_ARG, "null argument");
     *out = nullptr;
     if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
-    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT))
+    constexpr unsigned kDecomp = MDFFT_PLAN_DECOMP_SLAB | MDFFT_PLAN_DECOMP_PENCIL | MDFFT_PLAN_DECOMP_VOLUMETRIC;
+    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT | kDecomp))
         return fail(MDFFT_E_ARG, "unknown flag");
+    const unsigned decomp = flags & kDecomp;
+    if (decomp & (decomp - 1)) return fail(MDFFT_E_ARG, "at most one MDFFT_PLAN_DECOMP_* flag");
     if (dt != MDFFT_C64 && dt != MDFFT_C128 && dt != MDFFT_C64_TC_FP16 && dt != MDFFT_C64_TC_BF16)
         return fail(MDFFT_E_ARG, "unknown dtype");
     mdfft_plan_s *p = new (std::nothrow) mdfft_plan_s;
@@ -360,6 +397,16 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
             return fail(MDFFT_E_UNSUPPORTED, "order search: " + err);
         }
     }
+    if (decomp) {
+        const int kind = decomp == MDFFT_PLAN_DECOMP_SLAB     ? pl::kSlab
+                         : decomp == MDFFT_PLAN_DECOMP_PENCIL ? pl::kPencil
+                                                              : pl::kVolumetric;
+        std::string err;
+        if (!pl::block_decomposition(M, p->N, P, kind, p->order, p->bd, err)) {
+            release(p);
+            return fail(MDFFT_E_RANGE, err);
+        }
+    }
     const bool host_only = flags & MDFFT_PLAN_HOST_ONLY;
     if (!host_only) {
         // every axis is transformed once: its line length must be built
@@ -392,13 +439,24 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
             off += (entries * p->elem + 255) / 256 * 256;
         }
         p->tw_bytes = off;
-        cudaError_t e = cudaMalloc(&p->tw, off + 256);  // + the device error flag
+        // + the device error flag, + the owner tables of a comparison method
+        const std::vector<int64_t> owners = owner_tables(p);
+        cudaError_t e = cudaMalloc(&p->tw, off + 256 + owners.size() * sizeof(int64_t));
         if (e != cudaSuccess) {
             release(p);
             return cuda_fail(e, "cudaMalloc twiddles");
         }
         p->err = reinterpret_cast<int *>((char *)p->tw + off);
         cudaMemset(p->err, 0, sizeof(int));
+        if (!owners.empty()) {
+            const int64_t *tab = reinterpret_cast<const int64_t *>((char *)p->tw + off + 256);
+            e = cudaMemcpy((void *)tab, owners.data(), owners.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                release(p);
+                return cuda_fail(e, "owner tables");
+            }
+            set_block_owners(p, tab);
+        }
         for (int s = 0; s < M; ++s) {
             const int64_t n = p->pass[s].n;
             const int entries = std::max(1, mdfft::tw_entries(p->pass[s].k.plan));
@@ -457,18 +515,21 @@ mdfft_status mdfft_comm_volume(mdfft_plan_t p, mdfft_comm *out) {
         pl::Layout nat;
         nat.M = M;
         for (int i = 0; i < M; ++i) nat.axis[i] = i;
+        const bool rowwise = p->bd.kind == pl::kRowwise;
         for (int s = 0; s + 1 < M; ++s) {
-            c.per_transition[s] = pl::transition_amount(M, p->N, p->P, p->order[s], p->order[s + 1]);
+            c.per_transition[s] = rowwise ? pl::transition_amount(M, p->N, p->P, p->order[s], p->order[s + 1])
+                                          : pl::block_transition_amount(M, p->N, p->P, p->bd, s);
             c.total += c.per_transition[s];
         }
-        c.final_to_natural = pl::transition_amount(M, p->N, p->P, p->order[M - 1], nat);
+        c.final_to_natural = rowwise ? pl::transition_amount(M, p->N, p->P, p->order[M - 1], nat) : 0;
         c.paper_total = c.total;
         for (int s = 0; s < M; ++s) {
-            c.split_line[s] = pl::split_line_amount(M, p->N, p->P, p->order[s]);
+            c.split_line[s] = rowwise ? pl::split_line_amount(M, p->N, p->P, p->order[s])
+                                      : pl::block_split_amount(M, p->N, p->bd, p->order, s);
             c.paper_total += c.split_line[s];
             int64_t d[pl::kMaxDims];
             pl::layout_dims(p->order[s], p->N, d);
-            c.regime[s] = pl::regime(M, d, p->P);
+            c.regime[s] = rowwise ? pl::regime(M, d, p->P) : p->bd.k;
         }
         // Sec. 4 closed forms for the same T and Np
         const double T = (double)p->T, P = (double)p->P, nan = std::nan("");
@@ -490,6 +551,7 @@ mdfft_status mdfft_chunk(mdfft_plan_t p, int step, int64_t pid, int64_t *xs, int
     if (!p || !xs || !xe) return fail(MDFFT_E_ARG, "null argument");
     if (step < 0 || step > p->M) return fail(MDFFT_E_ARG, "step out of range");
     if (pid < 0 || pid >= p->P) return fail(MDFFT_E_ARG, "pid out of range");
+    if (p->bd.kind != pl::kRowwise) return fail(MDFFT_E_ARG, "f_MD chunks belong to row-wise plans");
     pl::Layout L;
     L.M = p->M;
     for (int i = 0; i < p->M; ++i) L.axis[i] = step < p->M ? p->order[step].axis[i] : i;
@@ -506,12 +568,22 @@ mdfft_status mdfft_exchange_counts(mdfft_plan_t p, int step, int G, int64_t *cou
     if (!p || !counts) return fail(MDFFT_E_ARG, "null argument");
     if (step < 0 || step >= p->M) return fail(MDFFT_E_ARG, "step out of range");
     if (G < 1 || G > p->P) return fail(MDFFT_E_ARG, "G must be in [1, P]");
+    if (p->bd.kind != pl::kRowwise) return fail(MDFFT_E_ARG, "exchange counts are for row-wise plans");
     pl::Layout nat;
     nat.M = p->M;
     for (int i = 0; i < p->M; ++i) nat.axis[i] = i;
     const pl::Layout &A = p->order[step];
     const pl::Layout &B = step + 1 < p->M ? p->order[step + 1] : nat;
     pl::exchange_counts(p->M, p->N, p->P, A, B, G, counts);
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_block_grid(mdfft_plan_t p, int step, int64_t *q_axis) {
+    if (!p || !q_axis) return fail(MDFFT_E_ARG, "null argument");
+    if (p->bd.kind == pl::kRowwise) return fail(MDFFT_E_ARG, "row-wise plan: no block grid");
+    if (step < 0 || step >= p->M) return fail(MDFFT_E_ARG, "step out of range");
+    int64_t ps[pl::kMaxDims];
+    pl::block_axis_grid(p->bd, p->M, step, q_axis, ps);
     return MDFFT_OK;
 }
 

@@ -67,4 +67,5 @@ struct mdfft_plan_s {
     int64_t timed = 0;            // executions recorded since the last enable
     bool comm_ready = false;
     mdfft_comm comm{};
+    mdfft::planner::BlockDecomp bd;  // comparison method of the counted amounts (kind kRowwise: f_MD chunks)
 };

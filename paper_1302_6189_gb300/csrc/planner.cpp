@@ -365,5 +365,97 @@ bool heuristic_order(int M, const int64_t *N, int64_t P, std::vector<Layout> &or
     return have;
 }
 
+bool block_decomposition(int M, const int64_t *N, int64_t P, int kind, const std::vector<Layout> &order,
+                         BlockDecomp &bd, std::string &err) {
+    bd = BlockDecomp();
+    bd.kind = kind;
+    if (kind == kRowwise) return true;
+    if (kind != kSlab && kind != kPencil && kind != kVolumetric) {
+        err = "unknown decomposition";
+        return false;
+    }
+    const int k = kind == kVolumetric ? M : kind;
+    if (k > M || (kind == kPencil && M < 3)) {
+        err = "the pencil method needs M >= 3";
+        return false;
+    }
+    bd.k = k;
+    // P's prime factors, largest first, each to the cut with the smallest product
+    std::vector<int64_t> primes;
+    int64_t r = P;
+    for (int64_t f = 2; f <= r / f; ++f)
+        for (; r % f == 0; r /= f) primes.push_back(f);
+    if (r > 1) primes.push_back(r);
+    std::sort(primes.rbegin(), primes.rend());
+    for (int j = 0; j < k; ++j) bd.q[j] = 1;
+    for (int64_t f : primes) {
+        int lo = 0;
+        for (int j = 1; j < k; ++j)
+            if (bd.q[j] < bd.q[lo]) lo = j;
+        bd.q[lo] *= f;
+    }
+    static const char *names[] = {"", "slab", "pencil", "volumetric"};
+    for (int s = 0; s < M; ++s) {
+        const int f = order[s].axis[M - 1];
+        for (int j = 0; j < k; ++j) {
+            if (s == 0)
+                bd.cut[0][j] = j;
+            else {
+                const int prev = bd.cut[s - 1][j];
+                bd.cut[s][j] = (k < M && prev == f) ? order[s - 1].axis[M - 1] : prev;
+            }
+            if (k < M && bd.cut[s][j] == f) {
+                err = std::string("the ") + names[kind] + " method cannot start by transforming a cut axis";
+                return false;
+            }
+            if (bd.q[j] > N[bd.cut[s][j]]) {
+                err = std::string("the ") + names[kind] + " method cuts an axis of " +
+                      std::to_string(N[bd.cut[s][j]]) + " points into " + std::to_string(bd.q[j]) + " blocks";
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+void block_axis_grid(const BlockDecomp &bd, int M, int s, int64_t *q_axis, int64_t *ps_axis) {
+    for (int a = 0; a < M; ++a) q_axis[a] = 1, ps_axis[a] = 0;
+    int64_t ps = 1;
+    for (int j = bd.k - 1; j >= 0; --j) {
+        q_axis[bd.cut[s][j]] = bd.q[j];
+        ps_axis[bd.cut[s][j]] = ps;
+        ps *= bd.q[j];
+    }
+}
+
+int64_t block_transition_amount(int M, const int64_t *N, int64_t P, const BlockDecomp &bd, int s) {
+    int64_t qa[kMaxDims], pa[kMaxDims], qb[kMaxDims], pb[kMaxDims];
+    block_axis_grid(bd, M, s, qa, pa);
+    block_axis_grid(bd, M, s + 1, qb, pb);
+    int64_t T = 1;
+    for (int a = 0; a < M; ++a) T *= N[a];
+    int64_t kept = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        int64_t v = 1;
+        for (int a = 0; a < M && v; ++a) {
+            // block of process p along axis a in either step; [lo, hi) points
+            const int64_t ba = qa[a] > 1 ? (p / pa[a]) % qa[a] : 0, bb = qb[a] > 1 ? (p / pb[a]) % qb[a] : 0;
+            const int64_t lo = std::max(ba * N[a] / qa[a], bb * N[a] / qb[a]);
+            const int64_t hi = std::min((ba + 1) * N[a] / qa[a], (bb + 1) * N[a] / qb[a]);
+            v *= hi > lo ? hi - lo : 0;
+        }
+        kept += v;
+    }
+    return T - kept;
+}
+
+int64_t block_split_amount(int M, const int64_t *N, const BlockDecomp &bd, const std::vector<Layout> &order, int s) {
+    int64_t q[kMaxDims], ps[kMaxDims];
+    block_axis_grid(bd, M, s, q, ps);
+    int64_t T = 1;
+    for (int a = 0; a < M; ++a) T *= N[a];
+    return T * (q[order[s].axis[M - 1]] - 1);
+}
+
 }  // namespace planner
 }  // namespace mdfft

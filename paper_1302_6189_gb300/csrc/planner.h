@@ -76,5 +76,38 @@ void exchange_counts(int M, const int64_t *N, int64_t P, const Layout &A, const 
 bool heuristic_order(int M, const int64_t *N, int64_t P, std::vector<Layout> &order, int64_t &total,
                      std::string &err);
 
+// The comparison methods of Sec. 4 as block decompositions.  k axes are cut
+// at a time (1: the 1-D or slab method, 2: the 2-D or pencil method, M: the
+// volumetric M-D methods); step s transforms the last axis of order[s].
+// With k < M the transformed axis is never cut: when the next step's axis is
+// cut, that cut moves to the axis just transformed (the methods' transposes).
+// Readings: the first step cuts the k slowest axes; P is split over the cuts
+// as evenly as possible (prime factors, largest first, each to the cut with
+// the smallest product, the first on ties); cut 0 varies slowest in the
+// process id; a cut of n points into q blocks gives block j the points
+// [floor(j n / q), floor((j + 1) n / q)) and needs q <= n.
+enum BlockKind { kRowwise = 0, kSlab = 1, kPencil = 2, kVolumetric = 3 };
+
+struct BlockDecomp {
+    int kind = kRowwise;
+    int k = 0;                           // cut axes per step
+    int64_t q[kMaxDims] = {0};           // blocks of cut j
+    int cut[kMaxDims][kMaxDims] = {{0}}; // [step][j]: natural axis of cut j
+};
+
+bool block_decomposition(int M, const int64_t *N, int64_t P, int kind, const std::vector<Layout> &order,
+                         BlockDecomp &bd, std::string &err);
+
+// Blocks along every natural axis in step s (1: not cut) and the process-id
+// stride of that axis (0: not cut).
+void block_axis_grid(const BlockDecomp &bd, int M, int s, int64_t *q_axis, int64_t *ps_axis);
+
+// Points whose owner differs between steps s and s+1 (box intersection per process).
+int64_t block_transition_amount(int M, const int64_t *N, int64_t P, const BlockDecomp &bd, int s);
+
+// Lines of step s shared by several owners, each gathering the whole line:
+// sum over lines of N_axis (owners - 1) = T (q - 1) when the axis is cut.
+int64_t block_split_amount(int M, const int64_t *N, const BlockDecomp &bd, const std::vector<Layout> &order, int s);
+
 }  // namespace planner
 }  // namespace mdfft

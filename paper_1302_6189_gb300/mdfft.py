@@ -23,6 +23,9 @@ MDFFT_OK, MDFFT_E_ARG, MDFFT_E_ORDER, MDFFT_E_RANGE = 0, -1, -2, -3
 MDFFT_E_NOMEM, MDFFT_E_CUDA, MDFFT_E_TIMEOUT, MDFFT_E_UNSUPPORTED = -4, -5, -6, -7
 MDFFT_C64, MDFFT_C128, MDFFT_C64_TC_FP16, MDFFT_C64_TC_BF16 = 0, 1, 2, 3
 MDFFT_PLAN_HOST_ONLY, MDFFT_PLAN_INPLACE, MDFFT_PLAN_PERSISTENT = 0x1, 0x2, 0x4
+MDFFT_PLAN_DECOMP_SLAB, MDFFT_PLAN_DECOMP_PENCIL, MDFFT_PLAN_DECOMP_VOLUMETRIC = 0x10, 0x20, 0x40
+DECOMPOSITIONS = {"rowwise": 0, "slab": MDFFT_PLAN_DECOMP_SLAB, "pencil": MDFFT_PLAN_DECOMP_PENCIL,
+                  "volumetric": MDFFT_PLAN_DECOMP_VOLUMETRIC}
 DTYPES = {"c64": MDFFT_C64, "c128": MDFFT_C128, "c64_tc_fp16": MDFFT_C64_TC_FP16,
           "c64_tc_bf16": MDFFT_C64_TC_BF16}
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_ORDER", -3: "E_RANGE", -4: "E_NOMEM", -5: "E_CUDA",
@@ -59,6 +62,7 @@ SIGNATURES = {
     "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
     "mdfft_plan_order": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_exchange_counts": (c_int, [c_void_p, c_int, c_int, P_(i64)]),
+    "mdfft_block_grid": (c_int, [c_void_p, c_int, P_(i64)]),
     "mdfft_order_search": (c_int, [c_int, P_(i64), i64, c_int, P_(c_int), P_(i64)]),
     "mdfft_order_heuristic": (c_int, [c_int, P_(i64), i64, P_(c_int), P_(i64)]),
     "mdfft_pass_timing": (c_int, [c_void_p, c_int]),
@@ -180,6 +184,12 @@ def mdfft_exchange_counts(plan, step, G):
     arr = (i64 * (G * G))()
     _check(_lib.mdfft_exchange_counts(plan, int(step), int(G), arr), "mdfft_exchange_counts")
     return [list(arr[g * G:(g + 1) * G]) for g in range(G)]
+
+
+def mdfft_block_grid(plan, step, M):
+    arr = (i64 * M)()
+    _check(_lib.mdfft_block_grid(plan, int(step), arr), "mdfft_block_grid")
+    return list(arr)
 
 
 def mdfft_plan_order(plan, M):
@@ -396,6 +406,10 @@ class Plan:
 
     def comm_volume(self):
         return mdfft_comm_volume(self.handle, self.M)
+
+    def block_grid(self, step):
+        """Blocks per natural axis in a step (plans with an MDFFT_PLAN_DECOMP_* flag)."""
+        return mdfft_block_grid(self.handle, step, self.M)
 
     def order(self):
         return mdfft_plan_order(self.handle, self.M)

@@ -188,6 +188,37 @@ def test_device_counts_match_oracle_bit_exact(shape, Ps):
             check(y.cpu().numpy(), ref_y, "c64", "counted")
 
 
+@pytest.mark.parametrize("shape,kind,Ps", [((8, 12, 10), "slab", (3, 8)), ((8, 12, 10), "pencil", (6, 16, 40)),
+                                           ((8, 12, 10), "volumetric", (12, 60, 960)),
+                                           ((6, 8, 4, 5), "pencil", (4, 12)), ((6, 8, 4, 5), "volumetric", (24, 120)),
+                                           ((64, 64, 64), "pencil", (16, 4096)),
+                                           ((64, 64, 64), "volumetric", (8192, 262144))])
+def test_device_counts_of_the_comparison_methods(shape, kind, Ps):
+    # the Sec. 4 methods through the same passes: counts equal the oracle's
+    # point-by-point ones, the spectrum is bit-identical to the row-wise plan's
+    M = len(shape)
+    orders = oracle.enumerate_orders(M, cap=3000)
+    rng = np.random.default_rng(12)
+    x = torch.from_numpy(si.uniform_complex(shape, 91).astype(np.complex64)).to(DEV)
+    for P in Ps:
+        for idx in rng.choice(len(orders), size=min(len(orders), 4), replace=False):
+            o = orders[idx]
+            axes = [L[-1] for L in o]
+            try:
+                ref = oracle.block_volume(shape, P, kind, axes)
+            except ValueError:
+                continue  # this order moves a cut onto an axis with fewer points
+            with md.Plan(shape, P, o, "c64", md.DECOMPOSITIONS[kind]) as plan, md.Plan(shape, P, o, "c64") as rw:
+                y, counts = plan.exec_counted(x)
+                y_rw = rw.exec(x)
+                torch.cuda.synchronize()
+                got = counts.cpu().tolist()
+            assert got[: M - 1] == ref["per_transition"], (kind, P, o)
+            assert got[M - 1] == 0
+            assert got[M:] == ref["split_line"], (kind, P, o)
+            assert torch.equal(y, y_rw)
+
+
 # ------------------------------------------------------------------ full-size configurations
 
 _REF = {}

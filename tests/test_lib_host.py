@@ -188,3 +188,91 @@ def test_heuristic_for_six_to_eight_dims():
             assert md.mdfft_plan_order(h, len(N)) == md.mdfft_order_heuristic(N, 4)[0]
         finally:
             md.mdfft_destroy(h)
+
+
+# ----------------------------------------------------------------------------- comparison methods (Sec. 4)
+
+def _fft_axes(order):
+    return [L[-1] for L in oracle.parse_order(order)]
+
+
+BLOCK_CASES = [((8, 8, 8), "slab", (2, 3, 8)), ((6, 5, 4), "slab", (2, 4, 5)),
+               ((8, 8, 8), "pencil", (2, 4, 6, 12, 16, 64)), ((12, 10, 9), "pencil", (6, 9, 30, 90)),
+               ((8, 8, 8), "volumetric", (2, 8, 12, 64, 100, 512)), ((6, 5, 4), "volumetric", (6, 30, 60)),
+               ((4, 6, 5, 2), "slab", (2, 4)), ((4, 6, 5, 2), "pencil", (4, 12, 24)),
+               ((4, 6, 5, 2), "volumetric", (8, 24, 240)), ((3, 4, 2, 2, 3), "volumetric", (6, 36)),
+               ((3, 4, 2, 2, 3), "pencil", (6, 12))]
+
+
+@pytest.mark.parametrize("N,kind,Ps", BLOCK_CASES, ids=lambda v: str(v))
+def test_comparison_methods_match_the_oracle(N, kind, Ps):
+    M = len(N)
+    rng = np.random.default_rng(45)
+    orders = oracle.enumerate_orders(M, cap=2000)
+    picks = [orders[0]] + [orders[i] for i in rng.choice(len(orders), size=min(4, len(orders) - 1), replace=False)]
+    checked = refused = 0
+    for o in picks:
+        order = oracle.format_order(o)
+        for P in Ps:
+            try:
+                ref = oracle.block_volume(N, P, kind, _fft_axes(order))
+            except ValueError:  # a cut with more blocks than points: both sides refuse
+                with pytest.raises(md.MdfftError) as e:
+                    md.mdfft_plan(N, P, order, "c64", HOST | md.DECOMPOSITIONS[kind])
+                assert e.value.status == md.mdfft.MDFFT_E_RANGE
+                refused += 1
+                continue
+            h = md.mdfft_plan(N, P, order, "c64", HOST | md.DECOMPOSITIONS[kind])
+            checked += 1
+            try:
+                got = md.mdfft_comm_volume(h, M)
+                for key in ("per_transition", "total", "split_line", "paper_total"):
+                    assert got[key] == ref[key], (order, P, key)
+                assert got["final_to_natural"] == 0
+                assert [md.mdfft_block_grid(h, s, M) for s in range(M)] == ref["q"]
+            finally:
+                md.mdfft_destroy(h)
+    assert checked >= len(Ps)
+
+
+def test_comparison_method_errors():
+    N = (8, 8, 8)
+    with pytest.raises(md.MdfftError) as e:
+        md.mdfft_plan(N, 16, None, "c64", HOST | md.MDFFT_PLAN_DECOMP_SLAB)  # 16 blocks of 8 points
+    assert e.value.status == md.mdfft.MDFFT_E_RANGE
+    with pytest.raises(md.MdfftError) as e:
+        md.mdfft_plan(N, 4, None, "c64", HOST | md.MDFFT_PLAN_DECOMP_SLAB | md.MDFFT_PLAN_DECOMP_PENCIL)
+    assert e.value.status == md.mdfft.MDFFT_E_ARG
+    with pytest.raises(md.MdfftError):
+        md.mdfft_plan((8, 8), 4, None, "c64", HOST | md.MDFFT_PLAN_DECOMP_PENCIL)  # needs M >= 3
+    h = md.mdfft_plan(N, 4, None, "c64", HOST | md.MDFFT_PLAN_DECOMP_PENCIL)
+    try:
+        with pytest.raises(md.MdfftError):
+            md.mdfft_chunk(h, 0, 0, 3)
+        with pytest.raises(md.MdfftError):
+            md.mdfft_exchange_counts(h, 0, 2)
+        with pytest.raises(md.MdfftError):
+            md.mdfft_block_grid(h, 3, 3)
+    finally:
+        md.mdfft_destroy(h)
+    h = _plan(N, 4)
+    try:
+        with pytest.raises(md.MdfftError):
+            md.mdfft_block_grid(h, 0, 3)  # row-wise plan
+    finally:
+        md.mdfft_destroy(h)
+
+
+def test_comparison_methods_reach_the_closed_forms_at_64_cubed():
+    # Fig. 7's setting: every method at the process counts where its closed form is exact
+    N = (64, 64, 64)
+    for kind, Ps, closed in (("slab", (2, 16, 64), lambda P: oracle.amount_slab(64, P)),
+                             ("pencil", (4, 16, 64, 256, 1024, 4096), lambda P: oracle.amount_pencil(64, P)),
+                             ("volumetric", (8, 64, 512, 4096, 32768, 262144),
+                              lambda P: oracle.amount_volumetric(3, 64, P))):
+        for P in Ps:
+            h = md.mdfft_plan(N, P, None, "c64", HOST | md.DECOMPOSITIONS[kind])
+            try:
+                assert md.mdfft_comm_volume(h, 3)["paper_total"] == pytest.approx(closed(P), rel=1e-14), (kind, P)
+            finally:
+                md.mdfft_destroy(h)
