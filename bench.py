@@ -54,8 +54,9 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="skip the per-order / complex128 table")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-case", action="store_true",
-                    help="one warm-up and one profiled forward transform of one 256^3 complex64 volume "
+                    help="one warm-up and one profiled forward transform of a batch of 256^3 volumes "
                          "(3 + 3 pass launches), for ncu captures")
+    ap.add_argument("--profile-batch", type=int, default=8, help="volumes per launch in --profile-case")
     ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
     ap.add_argument("--serving-only", type=int, default=0, metavar="REQUESTS",
                     help="run only the serving study with this many requests and print it")
@@ -272,24 +273,25 @@ def run_ours(args):
     elem = 8
     per_transform, T = algorithmic_bytes(shape, elem)
     order, total_amount = mdfft_order_search(shape, P, 0)
-    plan = Plan(shape, P, order, "c64")
+    # one batched plan: every pass is one launch over the tiles of all B volumes
+    plan = Plan(shape, P, order, "c64", batch=B)
     comm = plan.comm_volume()
 
-    xs = [torch.from_numpy(si.uniform_complex(shape, si.SEEDS["cube256"] + i, np.complex64)).to(dev)
-          for i in range(B)]
-    ys = [torch.empty_like(xs[0]) for _ in range(B)]
-    zs = [torch.empty_like(xs[0]) for _ in range(B)]
+    xs = torch.empty((B,) + shape, dtype=torch.complex64, device=dev)
+    for i in range(B):
+        xs[i].copy_(torch.from_numpy(si.uniform_complex(shape, si.SEEDS["cube256"] + i, np.complex64)))
+    ys = torch.empty_like(xs)
+    zs = torch.empty_like(xs)
     stream = torch.cuda.current_stream(dev)
     nvtx = torch.cuda.nvtx
     nvtx.range_push("autotune")
-    tune_before, tune_after = plan.autotune(xs[0], ys[0], reps=20)
+    tune_before, tune_after = plan.autotune(xs, ys, reps=5)
     nvtx.range_pop()
     tuned = [{k: d[k] for k in ("threads", "tile_g", "tile_h", "ctas")} for d in plan.describe()]
 
     def step():
-        for i in range(B):
-            plan.exec(xs[i], ys[i], dir=-1)
-            plan.exec(ys[i], zs[i], dir=+1, normalize=True)
+        plan.exec(xs, ys, dir=-1)
+        plan.exec(ys, zs, dir=+1, normalize=True)
 
     nvtx.range_push("warmup")
     for _ in range(max(3, args.warmup)):
@@ -322,25 +324,24 @@ def run_ours(args):
     bytes_per_step = 2 * B * per_transform
     value = world * args.steps * bytes_per_step / (ms_max * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    launch_bytes = 2 * T * elem  # one pass: read and write the array once
+    launch_bytes = 2 * B * T * elem  # one pass: read and write the B arrays once
     avg_launch_ms = sum(pass_ms) / len(pass_ms)
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
     traffic = profile_traffic()
     # the bound the redistribution's access pattern puts on a pass: the same
     # loads and transposed stores without the butterflies
-    pattern_ms = [plan.pattern_probe(s_, xs[0], ys[0], reps=20) for s_ in range(3)]
+    pattern_ms = [plan.pattern_probe(s_, xs, ys, reps=5) for s_ in range(3)]
     pattern_gbs = launch_bytes / (sum(pattern_ms) / len(pattern_ms) * 1e-3) / 1e9
 
     # end to end: host (pinned) buffers through mdfft_exec_host, copies inside the timed region
-    hx = [xs[i].cpu().pin_memory() for i in range(B)]
-    hy = [torch.empty_like(hx[0]).pin_memory() for _ in range(B)]
-    hz = [torch.empty_like(hx[0]).pin_memory() for _ in range(B)]
-    din, dout = torch.empty_like(xs[0]), torch.empty_like(xs[0])
+    hx = xs.cpu().pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    hz = torch.empty_like(hx).pin_memory()
+    din, dout = torch.empty_like(xs), torch.empty_like(xs)
 
     def e2e_step():
-        for i in range(B):
-            plan.exec_host(hx[i], hy[i], din, dout, dir=-1)
-            plan.exec_host(hy[i], hz[i], din, dout, dir=+1, normalize=True)
+        plan.exec_host(hx, hy, din, dout, dir=-1)
+        plan.exec_host(hy, hz, din, dout, dir=+1, normalize=True)
 
     e2e_step()
     torch.cuda.synchronize(dev)
@@ -391,7 +392,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * B * T * elem, "steps": e_steps, "roundtrip_rel_l2": e2e_err,
                 "api": "mdfft_exec_host"},
         "clocks": clk,
-        "gpu_launches": args.steps * B * 2 * plan.launches(),
+        "gpu_launches": args.steps * 2 * plan.launches(),
         "kernel_source_sha256": kernel_hash(),
     }
     if extra is not None:
@@ -540,13 +541,17 @@ def profile_case(args):
 
     torch.cuda.set_device(0)
     npdt = np.complex128 if args.profile_dtype == "c128" else np.complex64
-    x = torch.from_numpy(si.uniform_complex(SHAPE, si.SEEDS["cube256"], npdt)).cuda()
-    with Plan(SHAPE, args.P, None, args.profile_dtype) as plan:
+    B = args.profile_batch
+    x = torch.empty((B,) + SHAPE if B > 1 else SHAPE, dtype=torch.from_numpy(np.zeros(1, npdt)).dtype,
+                    device="cuda")
+    for i in range(B):
+        (x[i] if B > 1 else x).copy_(torch.from_numpy(si.uniform_complex(SHAPE, si.SEEDS["cube256"] + i, npdt)))
+    with Plan(SHAPE, args.P, None, args.profile_dtype, batch=B) as plan:
         y = torch.empty_like(x)
         plan.exec(x, y)  # warm-up: launches 1-3
         plan.exec(x, y)  # profiled: launches 4-6
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": f"256^3 {args.profile_dtype} forward", "order": plan.order_str(),
+        print(json.dumps({"profile_case": f"{B} x 256^3 {args.profile_dtype} forward", "order": plan.order_str(),
                           "passes": plan.describe()}))
 
 

@@ -111,6 +111,21 @@ mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, 
                         mdfft_dtype dt, unsigned flags);
 
 /*
+ * mdfft_plan_batched -- as mdfft_plan for `batch` independent transforms of
+ * the same dims per execution (batch >= 1; mdfft_plan is batch = 1).  The
+ * arrays of mdfft_exec / mdfft_exec_counted / mdfft_exec_host then hold
+ * batch * N_1 ... N_M elements, transform v at element offset v * T, and the
+ * plan's workspace is that size too.  Each pass is one launch over the tiles
+ * of every transform of the batch (the batch is the outermost tile axis), so
+ * the partly filled last wave of CTAs is paid once per pass, not once per
+ * transform.  Counted executions add the amounts of all transforms; the
+ * amounts of mdfft_comm_volume are per transform.  batch * T must not exceed
+ * 2^40 (E_ARG).
+ */
+mdfft_status mdfft_plan_batched(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order,
+                                mdfft_dtype dt, unsigned flags, int64_t batch);
+
+/*
  * mdfft_exec -- run the plan: M fused passes, pass s doing the 1-D FFTs along
  * the last axis of layout s (Fig. 4, steps 1..M) and storing straight into
  * layout s+1 (the transposes of Fig. 4; the last one gives natural order).

@@ -180,6 +180,13 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
         a.nrest++;
         ps.ctas *= p->N[ax];
     }
+    if (p->batch > 1) {  // the transforms of a batch: one more axis, outermost, stride T in and out
+        a.rest_count[a.nrest] = p->batch;
+        a.rest_in[a.nrest] = p->T;
+        a.rest_out[a.nrest] = p->T;
+        a.nrest++;
+        ps.ctas *= p->batch;
+    }
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
@@ -276,7 +283,7 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
         return fail(MDFFT_E_ARG, "normalize = 1 is only defined for the inverse");
     size_t align = p->dt == MDFFT_C128 ? 16 : 8;
     if ((uintptr_t)in % align || (uintptr_t)out % align) return fail(MDFFT_E_ARG, "misaligned data pointer");
-    const size_t bytes = (size_t)p->T * p->elem;
+    const size_t bytes = (size_t)p->T * p->batch * p->elem;
     const bool inplace = in == out;
     if (inplace && !(p->flags & MDFFT_PLAN_INPLACE))
         return fail(MDFFT_E_ARG, "in == out needs a plan made with MDFFT_PLAN_INPLACE");
@@ -341,16 +348,22 @@ int mdfft_supported_length(int64_t n, mdfft_dtype dt) {
 
 mdfft_status mdfft_plan(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order, mdfft_dtype dt,
                         unsigned flags) {
-    return mdfft::detail::plan_create(out, M, N, P, order, dt, flags, true);
+    return mdfft::detail::plan_create(out, M, N, P, order, dt, flags, true, 1);
+}
+
+mdfft_status mdfft_plan_batched(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order,
+                                mdfft_dtype dt, unsigned flags, int64_t batch) {
+    return mdfft::detail::plan_create(out, M, N, P, order, dt, flags, true, batch);
 }
 
 }  // extern "C"
 
 mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order,
-                                        mdfft_dtype dt, unsigned flags, bool with_workspace) {
+                                        mdfft_dtype dt, unsigned flags, bool with_workspace, int64_t batch) {
     g_err.clear();
     if (!out || !N) return fail(MDFFT_E_ARG, "null argument");
     *out = nullptr;
+    if (batch < 1) return fail(MDFFT_E_ARG, "batch must be >= 1");
     if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
     constexpr unsigned kDecomp = MDFFT_PLAN_DECOMP_SLAB | MDFFT_PLAN_DECOMP_PENCIL | MDFFT_PLAN_DECOMP_VOLUMETRIC;
     if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT | kDecomp))
@@ -377,6 +390,11 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
         return fail(MDFFT_E_ARG, "grid too large");
     }
     p->T = (int64_t)T;
+    p->batch = batch;
+    if (T * (unsigned __int128)batch > ((unsigned __int128)1 << 40)) {
+        release(p);
+        return fail(MDFFT_E_ARG, "batch too large");
+    }
     if (P < 1 || P > p->T) {
         release(p);
         return fail(MDFFT_E_RANGE, "P must be in [1, N_1 ... N_M]");
@@ -463,7 +481,7 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
             twiddle_kernel<<<(unsigned)((entries + 255) / 256), 256>>>((char *)p->tw + p->pass[s].tw_offset, n,
                                                                        p->pass[s].k.plan, dt == MDFFT_C128);
         }
-        const size_t bytes = (size_t)p->T * p->elem;
+        const size_t bytes = (size_t)p->T * p->batch * p->elem;
         p->external_ws = !with_workspace;
         if (with_workspace && (e = cudaMalloc(&p->ws, bytes)) != cudaSuccess) {
             release(p);
@@ -669,7 +687,7 @@ mdfft_status mdfft_exec_host(mdfft_plan_t p, const void *in_host, void *out_host
     if (!p) return fail(MDFFT_E_ARG, "null plan");
     if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan cannot execute");
     if (!in_host || !out_host || !dev_in || !dev_out) return fail(MDFFT_E_ARG, "null pointer");
-    const size_t bytes = (size_t)p->T * p->elem;
+    const size_t bytes = (size_t)p->T * p->batch * p->elem;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(dev_in, in_host, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
@@ -685,7 +703,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
     if (!p || !in || !out) return fail(MDFFT_E_ARG, "null argument");
     if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan");
     if (reps < 1) return fail(MDFFT_E_ARG, "reps must be >= 1");
-    const size_t bytes = (size_t)p->T * p->elem;
+    const size_t bytes = (size_t)p->T * p->batch * p->elem;
     if (overlaps(in, out, bytes)) return fail(MDFFT_E_ARG, "in and out overlap");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
@@ -841,8 +859,8 @@ mdfft_status mdfft_plan_check(mdfft_plan_t p) {
 mdfft_status mdfft_workspace_size(mdfft_plan_t p, size_t *bytes) {
     if (!p || !bytes) return fail(MDFFT_E_ARG, "null argument");
     *bytes = 0;
-    if (p->ws) *bytes += (size_t)p->T * p->elem;
-    if (p->ws2) *bytes += (size_t)p->T * p->elem;
+    if (p->ws) *bytes += (size_t)p->T * p->batch * p->elem;
+    if (p->ws2) *bytes += (size_t)p->T * p->batch * p->elem;
     return MDFFT_OK;
 }
 

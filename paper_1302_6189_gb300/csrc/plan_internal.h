@@ -34,7 +34,7 @@ mdfft_status cuda_fail(cudaError_t e, const char *what);
 // mdfft_plan without the plan's own workspace (its owner supplies one per
 // execution, as the server does).  exec on such a plan is refused.
 mdfft_status plan_create(mdfft_plan_t *out, int M, const int64_t N[], int64_t P, const int *order, mdfft_dtype dt,
-                         unsigned flags, bool with_workspace);
+                         unsigned flags, bool with_workspace, int64_t batch);
 
 }  // namespace detail
 }  // namespace mdfft
@@ -53,6 +53,7 @@ struct mdfft_plan_s {
     int M = 0;
     int64_t N[MDFFT_MAX_DIMS] = {0};
     int64_t P = 0, T = 0;
+    int64_t batch = 1;            // transforms per execution, volume v at element offset v T
     mdfft_dtype dt = MDFFT_C64;
     unsigned flags = 0;
     size_t elem = 8;

@@ -298,7 +298,7 @@ mdfft_status get_plan(mdfft_server_t s, int M, const int64_t *N, mdfft_plan_t *o
     int64_t T = 1;
     for (int i = 0; i < M; ++i) T *= N[i];
     mdfft_plan_t p = nullptr;
-    mdfft_status st = mdfft::detail::plan_create(&p, M, N, std::min<int64_t>(s->P, T), nullptr, MDFFT_C64, 0, false);
+    mdfft_status st = mdfft::detail::plan_create(&p, M, N, std::min<int64_t>(s->P, T), nullptr, MDFFT_C64, 0, false, 1);
     if (st != MDFFT_OK) return st;
     s->plans[key] = p;
     std::vector<ServePass> rt(M);

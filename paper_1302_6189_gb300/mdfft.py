@@ -56,6 +56,7 @@ class MdfftServerStats(ctypes.Structure):
 
 SIGNATURES = {
     "mdfft_plan": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint]),
+    "mdfft_plan_batched": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint, i64]),
     "mdfft_exec": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_exec_counted": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "mdfft_comm_volume": (c_int, [c_void_p, P_(MdfftComm)]),
@@ -149,6 +150,16 @@ def mdfft_plan(N, P, order=None, dtype=MDFFT_C64, flags=0):
     oarr = None if order is None else (c_int * (M * M))(*parse_order(order, M))
     h = c_void_p()
     _check(_lib.mdfft_plan(ctypes.byref(h), M, dims, int(P), oarr, dt, int(flags)), "mdfft_plan")
+    return h
+
+
+def mdfft_plan_batched(N, P, order=None, dtype=MDFFT_C64, flags=0, batch=1):
+    dims, M = _dims(N)
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    oarr = None if order is None else (c_int * (M * M))(*parse_order(order, M))
+    h = c_void_p()
+    _check(_lib.mdfft_plan_batched(ctypes.byref(h), M, dims, int(P), oarr, dt, int(flags), int(batch)),
+           "mdfft_plan_batched")
     return h
 
 
@@ -362,15 +373,19 @@ _TORCH_DTYPE = {MDFFT_C64: "complex64", MDFFT_C128: "complex128",
 
 
 class Plan:
-    """A plan bound to torch CUDA tensors: ``Plan(shape, P, order, dtype)``."""
+    """A plan bound to torch CUDA tensors: ``Plan(shape, P, order, dtype)``.
+    With batch > 1 every tensor has shape (batch,) + shape: that many
+    independent transforms per execution."""
 
-    def __init__(self, shape, P, order=None, dtype="c64", flags=0):
-        self.shape = tuple(int(n) for n in shape)
-        self.M = len(self.shape)
+    def __init__(self, shape, P, order=None, dtype="c64", flags=0, batch=1):
+        self.M = len(tuple(shape))
         self.P = int(P)
         self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
         self.flags = int(flags)
-        self.handle = mdfft_plan(self.shape, P, order, self.dtype, flags)
+        self.batch = int(batch)
+        dims = tuple(int(n) for n in shape)
+        self.handle = mdfft_plan_batched(dims, P, order, self.dtype, flags, self.batch)
+        self.shape = dims if self.batch == 1 else (self.batch,) + dims
 
     def _stream(self, stream):
         import torch

@@ -276,3 +276,15 @@ def test_comparison_methods_reach_the_closed_forms_at_64_cubed():
                 assert md.mdfft_comm_volume(h, 3)["paper_total"] == pytest.approx(closed(P), rel=1e-14), (kind, P)
             finally:
                 md.mdfft_destroy(h)
+
+
+def test_batched_plan_arguments():
+    h = md.mdfft_plan_batched((8, 8, 8), 4, None, "c64", HOST, 6)
+    try:
+        assert md.mdfft_comm_volume(h, 3)["total"] == oracle.order_search((8, 8, 8), 4)["best"]  # per transform
+    finally:
+        md.mdfft_destroy(h)
+    for bad in (0, -1, 1 << 32):
+        with pytest.raises(md.MdfftError) as e:
+            md.mdfft_plan_batched((256, 256, 256), 4, None, "c64", HOST, bad)
+        assert e.value.status == md.mdfft.MDFFT_E_ARG
