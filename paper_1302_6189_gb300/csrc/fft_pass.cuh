@@ -19,8 +19,9 @@
 //            shared memory; every thread then owns one line and writes its
 //            k values, so a warp writes runs of Bg consecutive elements of
 //            the output layout's fastest axis.
-// Inverse transforms conjugate on load and on store (conj(DFT(conj x)) is
-// the exp(+2 pi i/N) sum); `scale` multiplies the stored values.
+// Inverse transforms conjugate the input of their first pass and the output
+// of their last one (conj(DFT(conj x)) is the exp(+2 pi i/N) sum; between
+// passes the two conjugations cancel); `scale` multiplies the stored values.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -60,7 +61,7 @@ struct PassArgs {
     int64_t Ng, Nh;                 // extents of g and h (ragged last tiles are masked)
     int64_t in_sg, in_sh;           // input strides of g and h
     int64_t out_sh, out_sf;         // output strides of h and f (g has output stride 1)
-    int conj;                       // 1: inverse
+    int conj;                       // inverse: bit 0 conjugates the loaded input, bit 1 the stored output
     double scale;                   // multiplies every stored value
     int64_t ntiles;                 // tiles of the pass (persistent kernels walk them)
     int *err;                       // persistent kernels: set to 1 if a bounded wait gave up (may be null)
@@ -426,13 +427,19 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
     unsigned long long moved = 0, split = 0;
     if (sok) {
         const int64_t obase = c.out_base + sbh * a.out_sh + sbg;
-        const Real sc = (Real)a.scale;
+        C *op = out + obase + (int64_t)k0 * a.out_sf;
+        const int64_t ostep = (int64_t)Cfg::TL * a.out_sf;
+        const C *bp = buf + k0 * Cfg::TROW + sl;
+        if (!(a.conj & 2) && a.scale == 1.0) {  // all passes but the last of an inverse
 #pragma unroll 4
-        for (int k = k0; k < N; k += Cfg::TL) {
-            C v = buf[k * Cfg::TROW + sl];
-            if (a.conj) v.y = -v.y;
-            v.x *= sc, v.y *= sc;
-            out[obase + k * a.out_sf] = v;
+            for (int k = k0; k < N; k += Cfg::TL, op += ostep, bp += Cfg::TL * Cfg::TROW) *op = *bp;
+        } else {
+            const Real sc = (Real)a.scale, sy = (a.conj & 2) ? -sc : sc;
+#pragma unroll 4
+            for (int k = k0; k < N; k += Cfg::TL, op += ostep, bp += Cfg::TL * Cfg::TROW) {
+                const C v = *bp;
+                *op = C{v.x * sc, v.y * sy};
+            }
         }
         if (a.moved) {  // count mode: owner of the point before and after the store
             const int64_t ib = lbase[sl];
@@ -494,7 +501,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
                 const int bg = l % a.Bg, bh = l / a.Bg;
                 if (l < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
                     C x = in[lbase[l] + i];
-                    if (a.conj) x.y = -x.y;
+                    if (a.conj & 1) x.y = -x.y;
                     buf[l * Cfg::PADN + padg<Cfg::PADG>(i)] = x;
                 }
             }
@@ -509,7 +516,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
         __syncthreads();
     } else {
         const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
-        Stages<Real, N, 0, 1, TC, THR>::run(buf, buf, tw, gsrc, line, tl, fok, a.conj != 0, active);
+        Stages<Real, N, 0, 1, TC, THR>::run(buf, buf, tw, gsrc, line, tl, fok, (a.conj & 1) != 0, active);
     }
     store_tile<Real, N, TC, THR>(a, buf, lbase, c, tid);
 }

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(PassCfg<float, N, 0, 0>::THREADS) fft_pass_pip
         auto refill = [&]() {  // buffer b has been read by the first stage
             if (warp == 0 && t + NBUF * G < ntiles) pipe_issue<N>(a, t + NBUF * G, mine, &bar[b], lane);
         };
-        Stages<float, N, 0, 1, 0, 0, 2>::run(buf, buf, tw, mine + (size_t)line * N, line, tl, fok, a.conj != 0, true,
+        Stages<float, N, 0, 1, 0, 0, 2>::run(buf, buf, tw, mine + (size_t)line * N, line, tl, fok, (a.conj & 1) != 0, true,
                                              refill);
         store_tile<float, N, 0, 0>(a, buf, lbase, c, tid);
         __syncthreads();  // the tile region and lbase are rewritten by the next tile

@@ -316,7 +316,7 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
         a.tw = (const char *)p->tw + ps.tw_offset;
         a.ntiles = ps.ctas;
         a.err = p->err;
-        a.conj = dir == 1;
+        a.conj = dir == 1 ? (s == 0 ? 1 : 0) | (s == M - 1 ? 2 : 0) : 0;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)p->T : 1.0;
         if (counts) {
             a.moved = reinterpret_cast<unsigned long long *>(counts + s);
@@ -1040,7 +1040,7 @@ extern "C" mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *
         a.in = src;
         a.out = dst[s];
         a.tw = scratch + (size_t)s * kNoallocTwiddleStride * elem;
-        a.conj = dir == 1;
+        a.conj = dir == 1 ? (s == 0 ? 1 : 0) | (s == M - 1 ? 2 : 0) : 0;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)T : 1.0;
         void *args[] = {&a};
         e = cudaLaunchKernel(k.fn, dim3((unsigned)pass[s].ctas), dim3(k.threads), args, k.smem, cs);

@@ -329,7 +329,7 @@ PassArgs pass_args(mdfft_server_t s, const Request *r, int pass) {
     a.in = src;
     a.out = dst;
     a.tw = (const char *)p->tw + p->pass[pass].tw_offset;
-    a.conj = r->dir == 1;
+    a.conj = r->dir == 1 ? (pass == 0 ? 1 : 0) | (pass == M - 1 ? 2 : 0) : 0;
     a.scale = (pass == M - 1 && r->normalize) ? 1.0 / (double)p->T : 1.0;
     return a;
 }
