@@ -160,7 +160,8 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int DATA = LINES * PADN > N * TROW ? LINES * PADN : N * TROW;
     static constexpr int TWN = tw_entries(plan) > 0 ? tw_entries(plan) : 1;  // twiddle entries
     static constexpr int BFRAG = TC ? 1024 * 4 / (int)sizeof(C) : 0;  // tensor-core B fragments (in C units)
-    static constexpr size_t SMEM = (size_t)(DATA + TWN + BFRAG) * sizeof(C) + (size_t)LINES * sizeof(int64_t);
+    // + the input offset of every tile line and the tile's coordinates (4 int64)
+    static constexpr size_t SMEM = (size_t)(DATA + TWN + BFRAG) * sizeof(C) + (size_t)(LINES + 4) * sizeof(int64_t);
     // first stage loads from HBM directly (tensor-core stages read shared memory)
     static constexpr bool DIRECT = TC == 0 && TL * (int)sizeof(C) >= 32;
 };
@@ -473,21 +474,28 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
     C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
     C *tw = buf + Cfg::DATA;
     int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);  // input offset of each tile line
+    TileCoord *shc = reinterpret_cast<TileCoord *>(lbase + Cfg::LINES);
     const bool active = tid < Cfg::THREADS;
 
     const C *in = reinterpret_cast<const C *>(a.in);
     const C *gtw = reinterpret_cast<const C *>(a.tw);
-    const TileCoord c = tile_coords(a, t);
 
+    // warp 0 alone turns the tile index into coordinates (64-bit divisions)
+    // and the lines' input offsets; the other warps read them after the barrier
+    if (tid < 32) {
+        const TileCoord w0 = tile_coords(a, t);
+        if (tid == 0) *shc = w0;
+        for (int l = tid; l < Cfg::LINES; l += 32) {
+            const int bg = l % a.Bg, bh = l / a.Bg;
+            lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
+        }
+    }
     if (active) {
         for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
         if constexpr (TC != 0) tc_build_bfrag<TC, Cfg::THREADS>(reinterpret_cast<uint32_t *>(tw + Cfg::TWN), tid);
-        if (tid < Cfg::LINES) {
-            const int bg = tid % a.Bg, bh = tid / a.Bg;
-            lbase[tid] = c.in_base + bg * a.in_sg + bh * a.in_sh;
-        }
     }
     __syncthreads();
+    const TileCoord c = *shc;
 
     // FFT role: thread (line, t) with t fastest
     const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
