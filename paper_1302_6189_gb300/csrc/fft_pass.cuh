@@ -311,6 +311,11 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
     static constexpr bool FIRST = SI == 0;
     static constexpr bool LAST = SI == Cfg::plan.S - 1;
     static constexpr int TWOFF = tw_offset(Cfg::plan, SI);
+    // a line's threads lie in one warp and a stage that is not the last reads
+    // and writes only its own line: warp barriers suffice around it (the last
+    // stage writes the transposed tile across lines and needs the CTA barrier;
+    // so does a landing buffer, refilled for every warp after the first stage)
+    static constexpr bool WARP_LOCAL = TC == 0 && 32 % Cfg::TL == 0 && SRC != 2;
 
     struct NoHook {
         __device__ __forceinline__ void operator()() const {}
@@ -358,7 +363,10 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
                 }
             }
         }
-        if constexpr (!(FIRST && SRC0 != 0)) __syncthreads();  // all reads of buf before any write
+        if constexpr (!(FIRST && SRC0 != 0)) {  // all reads of buf before any write
+            if constexpr (WARP_LOCAL && !LAST) __syncwarp();
+            else __syncthreads();
+        }
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int j = t + i * Cfg::TL;
@@ -380,7 +388,8 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
                 }
             }
         }
-        __syncthreads();
+        if constexpr (WARP_LOCAL && !LAST) __syncwarp();
+        else __syncthreads();
     }
 };
 
