@@ -241,7 +241,11 @@ mdfft_status mdfft_pass_times(mdfft_plan_t plan, float *ms_out, int cap, int *n_
  * for overlap; pageable memory works but the copies then block the host).
  * dev_in and dev_out are caller-owned device arrays of T elements (they may
  * be the same array only for MDFFT_PLAN_INPLACE plans).  The host buffers
- * must stay valid until the stream reaches the end of the call.
+ * must stay valid until the stream reaches the end of the call.  For a
+ * batched plan (all sizes times the batch) the work is pipelined per
+ * transform on three streams of the plan (copy in, passes, copy out), forked
+ * from and joined back into `stream`, so the two copy directions and the
+ * passes of neighbouring transforms overlap; results are identical.
  */
 mdfft_status mdfft_exec_host(mdfft_plan_t plan, const void *in_host, void *out_host, void *dev_in, void *dev_out,
                              int dir, int normalize, mdfft_stream_t stream);

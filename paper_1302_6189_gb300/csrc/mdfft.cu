@@ -264,6 +264,10 @@ void release(mdfft_plan_s *p) {
     if (p->ws2) cudaFree(p->ws2);
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaStream_t h : p->hs)
+        if (h) cudaStreamDestroy(h);
+    for (cudaEvent_t e : p->hev)
+        if (e) cudaEventDestroy(e);
     delete p;
 }
 
@@ -272,8 +276,11 @@ bool overlaps(const void *a, const void *b, size_t n) {
     return x < y + n && y < x + n;
 }
 
-mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, mdfft_stream_t stream,
-                       int64_t *counts) {
+mdfft_status launch_passes(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, cudaStream_t st,
+                           int64_t *counts, int64_t v);
+
+// Argument checks of an execution on device arrays (E_ARG with a message).
+mdfft_status check_exec(mdfft_plan_t p, const void *in, const void *out, int dir, int normalize, const int64_t *counts) {
     if (!p) return fail(MDFFT_E_ARG, "null plan");
     if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan cannot execute");
     if (p->external_ws) return fail(MDFFT_E_ARG, "plan has no workspace of its own");
@@ -292,29 +299,52 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
     for (int s = 0; s < p->M; ++s)  // persistent pipelined passes copy whole 16-byte units
         if (p->pass[s].k.persistent && (((uintptr_t)in % 16) || ((uintptr_t)out % 16)))
             return fail(MDFFT_E_ARG, "tuned pass kernels read whole 16-byte units: align in and out to 16 bytes");
+    return MDFFT_OK;
+}
 
+mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, mdfft_stream_t stream,
+                       int64_t *counts) {
+    mdfft_status cs = check_exec(p, in, out, dir, normalize, counts);
+    if (cs != MDFFT_OK) return cs;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (counts) {
+        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * p->M, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    return launch_passes(p, in, out, dir, normalize, st, counts, -1);
+}
+
+// The M passes on `st`: of the whole batch (v < 0) or of transform v alone
+// (the batch axis dropped, every array offset by v T elements; no timing).
+mdfft_status launch_passes(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, cudaStream_t st,
+                           int64_t *counts, int64_t v) {
     const int M = p->M;
+    const bool one = v >= 0 && p->batch > 1;
+    const size_t off = v >= 0 ? (size_t)v * (size_t)p->T * p->elem : 0;
+    auto at = [off](const void *b) { return b ? (void *)((char *)b + off) : nullptr; };
     // destination of every pass: the last one is `out`; going backwards the
     // buffers alternate so that no pass reads and writes the same array and
     // `in` is never written (unless in == out)
     void *dst[MDFFT_MAX_DIMS];
-    dst[M - 1] = out;
-    for (int s = M - 2; s >= 0; --s) dst[s] = (dst[s + 1] == out) ? p->ws : out;
-    if (dst[0] == in) dst[0] = p->ws2;  // in-place with an odd number of passes
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (counts) {
-        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * M, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    }
-    const void *src = in;
+    dst[M - 1] = at(out);
+    for (int s = M - 2; s >= 0; --s) dst[s] = (dst[s + 1] == at(out)) ? at(p->ws) : at(out);
+    if (dst[0] == at(in)) dst[0] = at(p->ws2);  // in-place with an odd number of passes
+    const void *src = at(in);
+    const bool timed = p->timing && v < 0;
     const int64_t slot = p->timed % MDFFT_TIMING_SLOTS;
     for (int s = 0; s < M; ++s) {
         Pass &ps = p->pass[s];
         PassArgs a = ps.args;
+        int64_t grid = ps.grid;
+        a.ntiles = ps.ctas;
+        if (one) {  // the batch is the outermost tile axis
+            a.nrest--;
+            a.ntiles = ps.ctas / p->batch;
+            grid = std::min<int64_t>(grid, a.ntiles);
+        }
         a.in = src;
         a.out = dst[s];
         a.tw = (const char *)p->tw + ps.tw_offset;
-        a.ntiles = ps.ctas;
         a.err = p->err;
         a.conj = dir == 1 ? (s == 0 ? 1 : 0) | (s == M - 1 ? 2 : 0) : 0;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)p->T : 1.0;
@@ -322,16 +352,56 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
             a.moved = reinterpret_cast<unsigned long long *>(counts + s);
             a.split = reinterpret_cast<unsigned long long *>(counts + M + s);
         }
-        if (p->timing) cudaEventRecord(p->ev[slot * (M + 1) + s], st);
+        if (timed) cudaEventRecord(p->ev[slot * (M + 1) + s], st);
         void *args[] = {&a};
-        cudaError_t e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)ps.grid), dim3(ps.k.threads), args, ps.k.smem, st);
+        cudaError_t e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)grid), dim3(ps.k.threads), args, ps.k.smem, st);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
         src = dst[s];
     }
-    if (p->timing) {
+    if (timed) {
         cudaEventRecord(p->ev[slot * (M + 1) + M], st);
         p->timed++;
     }
+    return MDFFT_OK;
+}
+
+// mdfft_exec_host for a batch: transform v's copy in, passes and copy out go
+// to three streams of the plan, so the copies of neighbouring transforms
+// overlap each other and the passes (both copy directions and the SMs busy at
+// once).  The transforms touch disjoint parts of every array; the caller's
+// stream is forked at the start and joined at the end.
+mdfft_status exec_host_pipelined(mdfft_plan_t p, const void *in_host, void *out_host, void *dev_in, void *dev_out,
+                                 int dir, int normalize, cudaStream_t st) {
+    mdfft_status cs = check_exec(p, dev_in, dev_out, dir, normalize, nullptr);
+    if (cs != MDFFT_OK) return cs;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!p->hs[i]) e = cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        if (!p->hev[i]) e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
+    cudaStream_t h2d = p->hs[0], comp = p->hs[1], d2h = p->hs[2];
+    cudaEvent_t fork = p->hev[0], copied = p->hev[1], computed = p->hev[2], done = p->hev[3];
+    const size_t vb = (size_t)p->T * p->elem;
+    e = cudaEventRecord(fork, st);
+    for (cudaStream_t h : p->hs)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h, fork, 0);
+    for (int64_t v = 0; v < p->batch && e == cudaSuccess; ++v) {
+        const size_t o = (size_t)v * vb;
+        e = cudaMemcpyAsync((char *)dev_in + o, (const char *)in_host + o, vb, cudaMemcpyHostToDevice, h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(copied, h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(comp, copied, 0);
+        if (e != cudaSuccess) break;
+        mdfft_status r = launch_passes(p, dev_in, dev_out, dir, normalize, comp, nullptr, v);
+        if (r != MDFFT_OK) return r;
+        e = cudaEventRecord(computed, comp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, computed, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char *)out_host + o, (const char *)dev_out + o, vb, cudaMemcpyDeviceToHost, d2h);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(done, d2h);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pipelined host execution");
     return MDFFT_OK;
 }
 
@@ -689,6 +759,7 @@ mdfft_status mdfft_exec_host(mdfft_plan_t p, const void *in_host, void *out_host
     if (!in_host || !out_host || !dev_in || !dev_out) return fail(MDFFT_E_ARG, "null pointer");
     const size_t bytes = (size_t)p->T * p->batch * p->elem;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->batch > 1) return exec_host_pipelined(p, in_host, out_host, dev_in, dev_out, dir, normalize, st);
     cudaError_t e = cudaMemcpyAsync(dev_in, in_host, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     mdfft_status r = exec_impl(p, dev_in, dev_out, dir, normalize, stream, nullptr);

@@ -69,4 +69,9 @@ struct mdfft_plan_s {
     bool comm_ready = false;
     mdfft_comm comm{};
     mdfft::planner::BlockDecomp bd;  // comparison method of the counted amounts (kind kRowwise: f_MD chunks)
+    // pipelined host execution of a batch (made on first use): streams for
+    // host-to-device copies, passes and device-to-host copies, and events
+    // (fork, copied in, computed, done)
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t hev[4] = {nullptr, nullptr, nullptr, nullptr};
 };

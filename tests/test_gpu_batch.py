@@ -89,3 +89,26 @@ def test_batch_autotune_and_persistent_kernel_keep_results():
         y = pp.exec(x)
         pp.check()
         assert torch.equal(y, want)
+
+
+@pytest.mark.parametrize("shape,P,B", [((32, 24, 40), 16, 4), ((8, 12, 10, 6), 12, 3)])
+def test_pipelined_host_execution(shape, P, B):
+    # copies and passes of neighbouring transforms on three streams: the same
+    # results as the device call, forward and normalised inverse, repeatedly
+    vols = _volumes(shape, B, "c64", 540)
+    x = torch.from_numpy(np.stack(vols)).to(DEV)
+    with md.Plan(shape, P, None, "c64", batch=B) as pb:
+        want = pb.exec(x)
+        back = pb.exec(want, dir=+1, normalize=True)
+        hx = x.cpu().pin_memory()
+        hy = torch.empty_like(hx).pin_memory()
+        hz = torch.empty_like(hx).pin_memory()
+        din, dout = torch.empty_like(x), torch.empty_like(x)
+        for _ in range(3):
+            pb.exec_host(hx, hy, din, dout)
+            pb.exec_host(hy, hz, din, dout, dir=+1, normalize=True)
+        torch.cuda.synchronize()
+        assert torch.equal(hy, want.cpu())
+        assert torch.equal(hz, back.cpu())
+    for i in range(B):
+        assert _rel(hz[i].numpy(), vols[i]) < TOL["c64"]
