@@ -455,9 +455,51 @@ def extra_table(dev, x, P):
                    "nominal_tflops_fp64": round(flops / (ms * 1e-3) / 1e12, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms]}
     res["precision_512cubed"] = precision_study(dev)
+    res["md_4d_5d"] = md_study(dev)
     res["decompositions"] = decomposition_study(dev)
     res["serving"] = serving_study(dev)
     return res
+
+
+def md_study(dev, reps=10):
+    """64^4 and 24^5 complex64 (U[-1,1) re/im), P in {64, 1024}, best and
+    worst orders: forward GB/s of a batched plan (4 volumes per launch, about
+    512 MiB per array) after autotuning, and the mean time of each pass."""
+    import numpy as np
+    import torch
+
+    import synth_inputs as si
+    from paper_1302_6189_gb300 import Plan, format_order, mdfft_order_search
+
+    out = {}
+    for shape in ((64, 64, 64, 64), (24, 24, 24, 24, 24)):
+        B = 4
+        M, T = len(shape), int(np.prod(shape))
+        x = torch.empty((B,) + shape, dtype=torch.complex64, device=dev)
+        for i in range(B):
+            x[i].copy_(torch.from_numpy(si.uniform_complex(shape, si.SEEDS["md_uniform"] + i, np.complex64)))
+        y = torch.empty_like(x)
+        for P in (64, 1024):
+            for want in (0, 1):
+                order, amount = mdfft_order_search(shape, P, want)
+                with Plan(shape, P, order, "c64", batch=B) as pl:
+                    pl.autotune(x, y, reps=3)
+                    for _ in range(3):
+                        pl.exec(x, y)
+                    pl.set_timing(True)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    for _ in range(reps):
+                        pl.exec(x, y)
+                    b.record()
+                    torch.cuda.synchronize(dev)
+                    ms = a.elapsed_time(b) / reps
+                    pass_ms, _ = pl.pass_times()
+                out[f"{'x'.join(map(str, shape))} P={P} {'worst' if want else 'best'}"] = {
+                    "order": format_order(order, M), "comm_points": amount,
+                    "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
+                    "pass_ms": [round(v, 4) for v in pass_ms]}
+    return out
 
 
 def decomposition_study(dev):

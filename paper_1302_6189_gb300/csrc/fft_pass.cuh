@@ -126,6 +126,15 @@ __host__ __device__ constexpr int pow2ceil(int x) {
     return p;
 }
 
+// complex64 lengths whose default CTA shape takes a power-of-two number of
+// threads per line (direct loads, warp-local stages) instead of N / (largest
+// radix): the ones where that measured faster on a GB300 (one pass over
+// 64 x 64 x N: N = 24 1.47x, 48 1.59x, 240 1.31x, 480 1.08x, 960 1.03x; the
+// other lengths with an odd factor measured slower with it).
+__host__ __device__ constexpr bool pow2_threads_default(int n) {
+    return n == 24 || n == 48 || n == 240 || n == 480 || n == 960;
+}
+
 template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     using C = typename Cx<Real>::T;
     static_assert(TC == 0 || sizeof(Real) == 4, "tensor-core stages are complex64 only");
@@ -133,7 +142,10 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static_assert(plan.S >= 0, "unsupported line length");  // S = 0: N = 1, a pure redistribution
     static constexpr int TL0 = N / plan.maxR;  // one butterfly per thread in the widest stage
     static constexpr int kMinLines = 128 / (int)sizeof(C);
-    static constexpr int TL = THR ? (pow2ceil(TL0) < THR / kMinLines ? pow2ceil(TL0) : THR / kMinLines) : TL0;
+    static constexpr bool POW2 = sizeof(Real) == 4 && TC == 0 && pow2_threads_default(N);
+    static constexpr int TL = THR    ? (pow2ceil(TL0) < THR / kMinLines ? pow2ceil(TL0) : THR / kMinLines)
+                              : POW2 ? pow2ceil(TL0)
+                                     : TL0;
     static constexpr int kTileElems = sizeof(Real) == 4 ? 4096 : 2048;
     // lines per tile: a power of two near kTileElems / N, at least enough for
     // 128-byte store runs (16 complex64 / 8 complex128), and a whole number
