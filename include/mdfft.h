@@ -84,6 +84,17 @@ typedef enum {
  * the cut with the smallest product); a cut of n points into q blocks needs
  * q <= n (else E_RANGE).  The output stays in the last step's decomposition.
  */
+/*
+ * Output layout.  MDFFT_PLAN_OUT_NATURAL (the default): the spectrum in
+ * natural row-major order (k_1 .. k_M), the last pass's store being the final
+ * transpose of Fig. 4.  MDFFT_PLAN_OUT_LAST_LAYOUT: the spectrum stays in the
+ * plan's last layout L_M (row-major with the axes in L_M's order, e.g. dims
+ * (N_b, N_c, N_a) for a last layout "bca"); the last pass then stores whole
+ * lines without transposing, and final_to_natural is 0.  Applies to both
+ * directions (the input is always natural).
+ */
+#define MDFFT_PLAN_OUT_NATURAL 0x0u
+#define MDFFT_PLAN_OUT_LAST_LAYOUT 0x80u
 #define MDFFT_PLAN_DECOMP_SLAB 0x10u
 #define MDFFT_PLAN_DECOMP_PENCIL 0x20u
 #define MDFFT_PLAN_DECOMP_VOLUMETRIC 0x40u

@@ -60,7 +60,9 @@ struct PassArgs {
     int Bg, Bh;                     // lines per tile along g and h
     int64_t Ng, Nh;                 // extents of g and h (ragged last tiles are masked)
     int64_t in_sg, in_sh;           // input strides of g and h
-    int64_t out_sh, out_sf;         // output strides of h and f (g has output stride 1)
+    int64_t out_sh, out_sf;         // output strides of h and f
+    int64_t out_sg;                 // output stride of g: 1, or N_f when the output keeps f fastest
+    int line_store;                 // 1: the output keeps f fastest (lines stored whole, no transpose)
     int conj;                       // inverse: bit 0 conjugates the loaded input, bit 1 the stored output
     double scale;                   // multiplies every stored value
     int64_t ntiles;                 // tiles of the pass (persistent kernels walk them)
@@ -421,7 +423,7 @@ __device__ __forceinline__ TileCoord tile_coords(const PassArgs &a, int64_t t) {
     t /= a.hblocks;
     c.g0 = gb * a.Bg, c.h0 = hb * a.Bh;
     c.in_base = c.g0 * a.in_sg + c.h0 * a.in_sh;
-    c.out_base = c.g0 + c.h0 * a.out_sh;
+    c.out_base = c.g0 * a.out_sg + c.h0 * a.out_sh;
     for (int i = 0; i < a.nrest; ++i) {
         const int64_t q = t % a.rest_count[i];
         t /= a.rest_count[i];
@@ -447,7 +449,26 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
     const int sbg = sl % a.Bg, sbh = sl / a.Bg;
     const bool sok = active && sl < a.Bg * a.Bh && c.g0 + sbg < a.Ng && c.h0 + sbh < a.Nh;
     unsigned long long moved = 0, split = 0;
-    if (sok) {
+    if (a.line_store) {  // the output keeps f fastest: every line is stored whole, k fastest across lanes
+        const Real sc = (Real)a.scale, sy = (a.conj & 2) ? -sc : sc;
+        const bool plain = !(a.conj & 2) && a.scale == 1.0;
+        for (int e = tid; e < Cfg::LINES * N && active; e += Cfg::THREADS) {
+            const int l = e / N, k = e % N;
+            const int bg = l % a.Bg, bh = l / a.Bg;
+            if (l < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
+                const int64_t o = c.out_base + bh * a.out_sh + bg * a.out_sg + k;
+                const C v = buf[k * Cfg::TROW + l];
+                out[o] = plain ? v : C{v.x * sc, v.y * sy};
+                if (a.moved) {
+                    moved += owner_of(a.own_in, lbase[l] + k) != owner_of(a.own_out, o);
+                    if (k == 0)
+                        split += (unsigned long long)N *
+                                ((owner_of(a.own_in, lbase[l] + N - 1) - owner_of(a.own_in, lbase[l])) /
+                                 a.own_in.line_div);
+                }
+            }
+        }
+    } else if (sok) {
         const int64_t obase = c.out_base + sbh * a.out_sh + sbg;
         C *op = out + obase + (int64_t)k0 * a.out_sf;
         const int64_t ostep = (int64_t)Cfg::TL * a.out_sf;

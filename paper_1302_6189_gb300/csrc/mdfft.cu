@@ -137,14 +137,17 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     pl::Layout nat;
     nat.M = M;
     for (int i = 0; i < M; ++i) nat.axis[i] = i;
-    const pl::Layout &Lo = (s + 1 < M) ? p->order[s + 1] : nat;
+    // the last pass stores natural order, or layout L_M itself (MDFFT_PLAN_OUT_LAST_LAYOUT)
+    const pl::Layout &Lo = (s + 1 < M) ? p->order[s + 1] : (p->flags & MDFFT_PLAN_OUT_LAST_LAYOUT) ? L : nat;
     Pass &ps = p->pass[s];
     ps.f = L.axis[M - 1];
     ps.g = Lo.axis[M - 1];
-    if (ps.g == ps.f) return fail(MDFFT_E_ORDER, "output layout keeps the transformed axis fastest");
+    const bool line_store = ps.g == ps.f;  // output keeps f fastest: lines stored whole
+    if (line_store && s + 1 < M) return fail(MDFFT_E_ORDER, "output layout keeps the transformed axis fastest");
+    if (line_store) ps.g = Lo.axis[M - 2];  // tile lines along the next axes of the layout
     ps.h = -1;
     for (int i = M - 2; i >= 0; --i)
-        if (Lo.axis[i] != ps.f) {
+        if (Lo.axis[i] != ps.f && Lo.axis[i] != ps.g) {
             ps.h = Lo.axis[i];
             break;
         }
@@ -167,7 +170,10 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     a.in_sh = ps.h >= 0 ? sin_[ps.h] : 0;
     a.out_sh = ps.h >= 0 ? sout[ps.h] : 0;
     a.out_sf = sout[ps.f];
-    if (sout[ps.g] != 1 || sin_[ps.f] != 1) return fail(MDFFT_E_ORDER, "internal: layout strides");
+    a.out_sg = sout[ps.g];
+    a.line_store = line_store ? 1 : 0;
+    if ((line_store ? sout[ps.f] : sout[ps.g]) != 1 || sin_[ps.f] != 1)
+        return fail(MDFFT_E_ORDER, "internal: layout strides");
     // remaining axes, fastest first in the output layout
     a.nrest = 0;
     ps.ctas = a.gblocks * a.hblocks;
@@ -436,7 +442,8 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
     if (batch < 1) return fail(MDFFT_E_ARG, "batch must be >= 1");
     if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
     constexpr unsigned kDecomp = MDFFT_PLAN_DECOMP_SLAB | MDFFT_PLAN_DECOMP_PENCIL | MDFFT_PLAN_DECOMP_VOLUMETRIC;
-    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT | kDecomp))
+    if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT | MDFFT_PLAN_OUT_LAST_LAYOUT |
+                  kDecomp))
         return fail(MDFFT_E_ARG, "unknown flag");
     const unsigned decomp = flags & kDecomp;
     if (decomp & (decomp - 1)) return fail(MDFFT_E_ARG, "at most one MDFFT_PLAN_DECOMP_* flag");
@@ -609,7 +616,9 @@ mdfft_status mdfft_comm_volume(mdfft_plan_t p, mdfft_comm *out) {
                                           : pl::block_transition_amount(M, p->N, p->P, p->bd, s);
             c.total += c.per_transition[s];
         }
-        c.final_to_natural = rowwise ? pl::transition_amount(M, p->N, p->P, p->order[M - 1], nat) : 0;
+        c.final_to_natural = rowwise && !(p->flags & MDFFT_PLAN_OUT_LAST_LAYOUT)
+                                 ? pl::transition_amount(M, p->N, p->P, p->order[M - 1], nat)
+                                 : 0;
         c.paper_total = c.total;
         for (int s = 0; s < M; ++s) {
             c.split_line[s] = rowwise ? pl::split_line_amount(M, p->N, p->P, p->order[s])
@@ -885,6 +894,7 @@ mdfft_status mdfft_pattern_probe(mdfft_plan_t p, int s, const void *in, void *ou
     if (s < 0 || s >= p->M || reps < 1) return fail(MDFFT_E_ARG, "bad pass index or reps");
     if (p->dt != MDFFT_C64) return fail(MDFFT_E_UNSUPPORTED, "complex64 plans only");
     const Pass &ps = p->pass[s];
+    if (ps.args.line_store) return fail(MDFFT_E_UNSUPPORTED, "the pass stores whole lines: no transpose to probe");
     PassKernel k;
     if (!mdfft::find_move_kernel_c64(ps.n, &k)) return fail(MDFFT_E_UNSUPPORTED, "no probe for this line length");
     PassArgs a;  // the default tiling of this length
@@ -1025,6 +1035,7 @@ mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dt
     a.in_sh = ps.h >= 0 ? sin_[ps.h] : 0;
     a.out_sh = ps.h >= 0 ? sout[ps.h] : 0;
     a.out_sf = sout[ps.f];
+    a.out_sg = 1;
     ps.ctas = a.gblocks * a.hblocks;
     for (int i = M - 1; i >= 0; --i) {
         int ax = Lo.axis[i];

@@ -24,6 +24,7 @@ MDFFT_E_NOMEM, MDFFT_E_CUDA, MDFFT_E_TIMEOUT, MDFFT_E_UNSUPPORTED = -4, -5, -6, 
 MDFFT_C64, MDFFT_C128, MDFFT_C64_TC_FP16, MDFFT_C64_TC_BF16 = 0, 1, 2, 3
 MDFFT_PLAN_HOST_ONLY, MDFFT_PLAN_INPLACE, MDFFT_PLAN_PERSISTENT = 0x1, 0x2, 0x4
 MDFFT_PLAN_DECOMP_SLAB, MDFFT_PLAN_DECOMP_PENCIL, MDFFT_PLAN_DECOMP_VOLUMETRIC = 0x10, 0x20, 0x40
+MDFFT_PLAN_OUT_NATURAL, MDFFT_PLAN_OUT_LAST_LAYOUT = 0x0, 0x80
 DECOMPOSITIONS = {"rowwise": 0, "slab": MDFFT_PLAN_DECOMP_SLAB, "pencil": MDFFT_PLAN_DECOMP_PENCIL,
                   "volumetric": MDFFT_PLAN_DECOMP_VOLUMETRIC}
 DTYPES = {"c64": MDFFT_C64, "c128": MDFFT_C128, "c64_tc_fp16": MDFFT_C64_TC_FP16,
@@ -386,24 +387,34 @@ class Plan:
         dims = tuple(int(n) for n in shape)
         self.handle = mdfft_plan_batched(dims, P, order, self.dtype, flags, self.batch)
         self.shape = dims if self.batch == 1 else (self.batch,) + dims
+        # MDFFT_PLAN_OUT_LAST_LAYOUT: the output's dims are in the last layout's axis order
+        out_dims = dims
+        if self.flags & MDFFT_PLAN_OUT_LAST_LAYOUT:
+            out_dims = tuple(dims[a] for a in mdfft_plan_order(self.handle, self.M)[-1])
+        self.out_shape = out_dims if self.batch == 1 else (self.batch,) + out_dims
 
     def _stream(self, stream):
         import torch
         s = torch.cuda.current_stream() if stream is None else stream
         return s.cuda_stream
 
-    def _check_tensor(self, t, name):
+    def _check_tensor(self, t, name, shape=None, cuda=True):
         import torch
         want = getattr(torch, _TORCH_DTYPE[self.dtype])
-        if not (t.is_cuda and t.dtype == want and t.is_contiguous() and tuple(t.shape) == self.shape):
-            raise ValueError(f"{name} must be a contiguous CUDA {want} tensor of shape {self.shape}")
+        shape = self.shape if shape is None else shape
+        if not (t.is_cuda == cuda and t.dtype == want and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"{name} must be a contiguous {'CUDA' if cuda else 'host'} {want} tensor of shape {shape}")
+
+    def _out(self, x, out):
+        import torch
+        if out is None:
+            out = torch.empty(self.out_shape, dtype=x.dtype, device=x.device)
+        self._check_tensor(out, "out", self.out_shape)
+        return out
 
     def exec(self, x, out=None, dir=-1, normalize=False, stream=None):
-        import torch
         self._check_tensor(x, "input")
-        if out is None:
-            out = torch.empty_like(x)
-        self._check_tensor(out, "out")
+        out = self._out(x, out)
         mdfft_exec(self.handle, x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
         return out
 
@@ -411,9 +422,7 @@ class Plan:
         """Returns (out, counts): counts is an int64 CUDA tensor of 2*M entries."""
         import torch
         self._check_tensor(x, "input")
-        if out is None:
-            out = torch.empty_like(x)
-        self._check_tensor(out, "out")
+        out = self._out(x, out)
         counts = torch.empty(2 * self.M, dtype=torch.int64, device=x.device)
         mdfft_exec_counted(self.handle, x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)),
                            self._stream(stream), counts.data_ptr())
@@ -447,8 +456,10 @@ class Plan:
 
     def exec_host(self, x_host, out_host, dev_in, dev_out, dir=-1, normalize=False, stream=None):
         """End to end on host tensors (pinned for async copies) via caller device buffers."""
-        for t, name in ((dev_in, "dev_in"), (dev_out, "dev_out")):
-            self._check_tensor(t, name)
+        self._check_tensor(dev_in, "dev_in")
+        self._check_tensor(dev_out, "dev_out", self.out_shape)
+        self._check_tensor(x_host, "x_host", cuda=False)
+        self._check_tensor(out_host, "out_host", self.out_shape, cuda=False)
         mdfft_exec_host(self.handle, x_host.data_ptr(), out_host.data_ptr(), dev_in.data_ptr(),
                         dev_out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
         return out_host
@@ -457,13 +468,13 @@ class Plan:
         """Pick the fastest kernel variant and tile shape per pass; returns
         (ms per pass before, after).  x is only read; scratch is overwritten."""
         self._check_tensor(x, "input")
-        self._check_tensor(scratch, "scratch")
+        self._check_tensor(scratch, "scratch", self.out_shape)
         return mdfft_plan_autotune(self.handle, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream), self.M)
 
     def pattern_probe(self, s, x, scratch, reps=10, stream=None):
         """ms per launch of a kernel that moves pass s's data like the pass, without the FFT."""
         self._check_tensor(x, "input")
-        self._check_tensor(scratch, "scratch")
+        self._check_tensor(scratch, "scratch", self.out_shape)
         return mdfft_pattern_probe(self.handle, s, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream))
 
     def check(self):

@@ -219,6 +219,46 @@ def test_device_counts_of_the_comparison_methods(shape, kind, Ps):
             assert torch.equal(y, y_rw)
 
 
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("shape,P,orders", [((20, 24, 12), 7, ORDERS3), ((8, 12, 10, 6), 16, None),
+                                            ((6, 5, 8, 4, 3), 12, None)])
+def test_output_in_the_last_layout(dt, shape, P, orders):
+    # MDFFT_PLAN_OUT_LAST_LAYOUT: the spectrum stays in layout L_M (the last
+    # pass stores whole lines); it is the natural-order result with the axes
+    # permuted into L_M, bit for bit, forward and normalised inverse
+    M = len(shape)
+    if orders is None:
+        orders = [oracle.format_order(o) for o in oracle.enumerate_orders(M, cap=400)[::97]]
+    x = si.uniform_complex(shape, 57)
+    xd = torch.from_numpy(np.ascontiguousarray(x.astype(NP[dt]))).to(DEV)
+    ref = oracle.fftn(x)
+    for order in orders:
+        last = oracle.parse_order(order)[-1]
+        with md.Plan(shape, P, order, dt, md.MDFFT_PLAN_OUT_LAST_LAYOUT) as pl, md.Plan(shape, P, order, dt) as pn:
+            assert pl.out_shape == tuple(shape[a] for a in last)
+            y = pl.exec(xd)
+            assert torch.equal(y, pn.exec(xd).permute(*last).contiguous())
+            yi = pl.exec(xd, dir=+1, normalize=True)
+            assert torch.equal(yi, pn.exec(xd, dir=+1, normalize=True).permute(*last).contiguous())
+            _, counts = pl.exec_counted(xd)
+            assert counts[M - 1].item() == 0 and pl.comm_volume()["final_to_natural"] == 0
+            assert counts[: M - 1].cpu().tolist() == pn.comm_volume()["per_transition"]
+        check(y.cpu().numpy(), np.transpose(ref, last), dt, f"{shape} {order}")
+
+
+def test_output_in_the_last_layout_batched_and_persistent():
+    shape, P, B = (32, 48, 64), 12, 3
+    x = torch.from_numpy(np.stack([si.uniform_complex(shape, 58 + i, np.complex64) for i in range(B)])).to(DEV)
+    with md.Plan(shape, P, None, "c64", batch=B) as pn:
+        want = pn.exec(x)
+        last = pn.order()[-1]
+    for flags in (md.MDFFT_PLAN_OUT_LAST_LAYOUT, md.MDFFT_PLAN_OUT_LAST_LAYOUT | md.MDFFT_PLAN_PERSISTENT):
+        with md.Plan(shape, P, None, "c64", flags, batch=B) as pl:
+            y = pl.exec(x)
+            pl.check()
+            assert torch.equal(y, want.permute(0, *[a + 1 for a in last]).contiguous())
+
+
 # ------------------------------------------------------------------ full-size configurations
 
 _REF = {}

@@ -288,3 +288,14 @@ def test_batched_plan_arguments():
         with pytest.raises(md.MdfftError) as e:
             md.mdfft_plan_batched((256, 256, 256), 4, None, "c64", HOST, bad)
         assert e.value.status == md.mdfft.MDFFT_E_ARG
+
+
+def test_output_in_the_last_layout_moves_nothing_at_the_end():
+    for order in ("abc->acb->bca", "abc->cab->cba"):
+        h = md.mdfft_plan((8, 6, 4), 6, order, "c64", HOST | md.MDFFT_PLAN_OUT_LAST_LAYOUT)
+        try:
+            cv = md.mdfft_comm_volume(h, 3)
+        finally:
+            md.mdfft_destroy(h)
+        ref = oracle.comm_volume((8, 6, 4), 6, order)
+        assert cv["final_to_natural"] == 0 and cv["per_transition"] == ref["per_transition"]
