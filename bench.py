@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -220,6 +221,26 @@ def oracle_fwd_inv_seconds(shape, reps, nthreads):
     return times
 
 
+def cpu_model():
+    try:  # lscpu names Arm cores too (its "Model name"); /proc/cpuinfo only has their part number there
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(shape, elem):
     nthreads = len(os.sched_getaffinity(0))
     # about 20 s of CPU work: one forward + inverse takes ~0.25 s on 16 cores
@@ -230,7 +251,7 @@ def cpu_baseline(shape, elem):
     return {"value": round(gbs, 3), "unit": "GB/s", "cores": nthreads, "kind": "oracle",
             "sample": f"{reps} x (forward + inverse) of one {'x'.join(map(str, shape))} volume, FP64 oracle "
                       f"(complex128) on {nthreads} host threads; bytes counted as for the complex64 GPU path",
-            "seconds": round(sum(times), 3)}
+            "seconds": round(sum(times), 3), "cpu": cpu_model()}
 
 
 def run_reference(args):
@@ -299,6 +320,11 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     nvtx.range_pop()
     err = float((torch.linalg.vector_norm(zs[0] - xs[0]) / torch.linalg.vector_norm(xs[0])).item())
+    # forward error of volume 0 against the complex128 GPU path of the same order
+    with Plan(shape, P, order, "c128") as p128:
+        ref = p128.exec(xs[0].to(torch.complex128))
+        fwd_err = float((torch.linalg.vector_norm(ys[0].to(torch.complex128) - ref) / torch.linalg.vector_norm(ref)).item())
+        del ref
 
     clocks = ClockSampler(local)
     plan.set_timing(True)
@@ -373,6 +399,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "pct_hbm_peak": round(100.0 * value / world / peak, 1),
+        "nominal_gflops": round(world * args.steps * 2 * B * 5.0 * T * math.log2(T) / (ms_max * 1e-3) / 1e9, 1),
+        "forward_rel_l2_vs_c128": fwd_err,
         "config": {"workload": "3-D complex64 FFT 256x256x256, forward + normalised inverse, batch of "
                                f"{B} distinct volumes per step",
                    "P": P, "order": format_order(order, 3), "regimes": comm["regime"],
@@ -386,7 +414,10 @@ def run_ours(args):
                      "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
                      "avg_launch_ms": round(avg_launch_ms, 5), "launches_timed": n_timed * 3,
                      "pattern_bound_gbs": round(pattern_gbs, 1), "frac_of_pattern": round(achieved / pattern_gbs, 4),
-                     "pass_ms": [round(v, 5) for v in pass_ms]},
+                     "pass_ms": [round(v, 5) for v in pass_ms],
+                     # ncu DRAM bytes of the M passes over the bytes of one full-array read + write
+                     "full_array_passes_per_transform": None if traffic is None else
+                     round(len(shape) * traffic / launch_bytes, 3)},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * B * T * elem,
                 "d2h_bytes_per_step": 2 * B * T * elem, "steps": e_steps, "roundtrip_rel_l2": e2e_err,
