@@ -151,14 +151,16 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int kTileElems = sizeof(Real) == 4 ? 4096 : 2048;
     // lines per tile: a power of two near kTileElems / N, at least enough for
     // 128-byte store runs (16 complex64 / 8 complex128), and a whole number
-    // of warps per CTA
+    // of warps per CTA; complex64 tiles grow only up to 256 threads (more,
+    // smaller CTAs per SM measured faster for every length it changes)
     // (tensor-core CTAs stay at <= 512 threads: their stages need ~100 registers)
     static constexpr int kMaxThreads = TC ? 512 : 1024;
+    static constexpr int kGrowThreads = (sizeof(Real) == 4 && TC == 0) ? 256 : kMaxThreads;
     static constexpr int lines_for() {
         if (THR) return THR / TL;
         int l = kMinLines;
         while (l > 1 && TL * l > kMaxThreads) l /= 2;
-        while (l < 256 && 2 * l * N <= kTileElems && 2 * TL * l <= kMaxThreads) l *= 2;
+        while (l < 256 && 2 * l * N <= kTileElems && 2 * TL * l <= kGrowThreads) l *= 2;
         while ((TL * l) % 32 != 0 && 2 * TL * l <= kMaxThreads) l *= 2;
         return l;
     }
