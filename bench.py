@@ -281,6 +281,43 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU arm
 
+def host_link_gbs(h_in, d_in, h_out, d_out, reps=3):
+    """Copy-engine bandwidth between pinned host memory and the GPU: each
+    direction alone and both at once (two streams), over the bench's buffers."""
+    import torch
+
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    cur = torch.cuda.current_stream()
+    nbytes = h_in.numel() * h_in.element_size()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        for _ in range(reps):
+            fn()
+        b.record(cur)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def both():
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    h2d = timed(lambda: d_in.copy_(h_in, non_blocking=True))
+    d2h = timed(lambda: h_out.copy_(d_out, non_blocking=True))
+    conc = timed(both)
+    return {"h2d_gbs": round(nbytes / (h2d * 1e-3) / 1e9, 1), "d2h_gbs": round(nbytes / (d2h * 1e-3) / 1e9, 1),
+            "concurrent_gbs": round(2 * nbytes / (conc * 1e-3) / 1e9, 1)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -383,6 +420,9 @@ def run_ours(args):
     e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = world * e_steps * bytes_per_step / (e_ms * 1e-3) / 1e9
     e2e_err = float((torch.linalg.vector_norm(hz[0] - hx[0]) / torch.linalg.vector_norm(hx[0])).item())
+    host_bytes = 4 * B * T * elem  # per step: two inputs in, two results out
+    link = host_link_gbs(hx, din, hy, dout)
+    link["frac_of_concurrent"] = round(host_bytes / (e_ms / e_steps * 1e-3) / 1e9 / link["concurrent_gbs"], 3)
 
     extra = None
     if not args.no_extra:
@@ -421,7 +461,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * B * T * elem,
                 "d2h_bytes_per_step": 2 * B * T * elem, "steps": e_steps, "roundtrip_rel_l2": e2e_err,
-                "api": "mdfft_exec_host"},
+                "api": "mdfft_exec_host", "host_link": link},
         "clocks": clk,
         "gpu_launches": args.steps * 2 * plan.launches(),
         "kernel_source_sha256": kernel_hash(),
