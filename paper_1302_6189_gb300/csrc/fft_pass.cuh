@@ -65,6 +65,7 @@ struct PassArgs {
     int line_store;                 // 1: the output keeps f fastest (lines stored whole, no transpose)
     int conj;                       // inverse: bit 0 conjugates the loaded input, bit 1 the stored output
     double scale;                   // multiplies every stored value
+    int scaled;                     // scale != 1 (set with scale, so the kernel tests an integer, not a double)
     int64_t ntiles;                 // tiles of the pass (persistent kernels walk them)
     int *err;                       // persistent kernels: set to 1 if a bounded wait gave up (may be null)
     unsigned long long *moved;      // count mode: points whose owner changes (null: off)
@@ -452,8 +453,8 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
     const bool sok = active && sl < a.Bg * a.Bh && c.g0 + sbg < a.Ng && c.h0 + sbh < a.Nh;
     unsigned long long moved = 0, split = 0;
     if (a.line_store) {  // the output keeps f fastest: every line is stored whole, k fastest across lanes
-        const Real sc = (Real)a.scale, sy = (a.conj & 2) ? -sc : sc;
-        const bool plain = !(a.conj & 2) && a.scale == 1.0;
+        const bool plain = !(a.conj & 2) && !a.scaled;
+        const Real sc = plain ? (Real)1 : (Real)a.scale, sy = (a.conj & 2) ? -sc : sc;
         for (int e = tid; e < Cfg::LINES * N && active; e += Cfg::THREADS) {
             const int l = e / N, k = e % N;
             const int bg = l % a.Bg, bh = l / a.Bg;
@@ -475,7 +476,7 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
         C *op = out + obase + (int64_t)k0 * a.out_sf;
         const int64_t ostep = (int64_t)Cfg::TL * a.out_sf;
         const C *bp = buf + k0 * Cfg::TROW + sl;
-        if (!(a.conj & 2) && a.scale == 1.0) {  // all passes but the last of an inverse
+        if (!(a.conj & 2) && !a.scaled) {  // all passes but the last of an inverse
 #pragma unroll 4
             for (int k = k0; k < N; k += Cfg::TL, op += ostep, bp += Cfg::TL * Cfg::TROW) *op = *bp;
         } else {

@@ -196,6 +196,7 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
+    a.scaled = 0;
     ps.grid = ps.ctas;
     return MDFFT_OK;
 }
@@ -354,6 +355,7 @@ mdfft_status launch_passes(mdfft_plan_t p, const void *in, void *out, int dir, i
         a.err = p->err;
         a.conj = dir == 1 ? (s == 0 ? 1 : 0) | (s == M - 1 ? 2 : 0) : 0;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)p->T : 1.0;
+        a.scaled = a.scale != 1.0;
         if (counts) {
             a.moved = reinterpret_cast<unsigned long long *>(counts + s);
             a.split = reinterpret_cast<unsigned long long *>(counts + M + s);
@@ -836,6 +838,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 a.out = out;
                 a.tw = (const char *)p->tw + ps.tw_offset;
                 a.scale = 1.0;
+                a.scaled = 0;
                 a.ntiles = cand.ctas;
                 a.err = p->err;
                 void *args[] = {&a};
@@ -900,7 +903,7 @@ mdfft_status mdfft_pattern_probe(mdfft_plan_t p, int s, const void *in, void *ou
     PassArgs a;  // the default tiling of this length
     int64_t ctas = 0;
     mdfft::detail::retile_pass(p, s, k.lines, &a, &ctas);
-    a.in = in, a.out = out, a.scale = 1.0, a.conj = 0, a.moved = nullptr, a.split = nullptr;
+    a.in = in, a.out = out, a.scale = 1.0, a.scaled = 0, a.conj = 0, a.moved = nullptr, a.split = nullptr;
     if (k.smem > 48 * 1024 &&
         cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
         return fail(MDFFT_E_CUDA, "cudaFuncSetAttribute");
@@ -1047,6 +1050,7 @@ mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dt
         ps.ctas *= N[ax];
     }
     a.scale = 1.0;
+    a.scaled = 0;
     return MDFFT_OK;
 }
 
@@ -1124,6 +1128,7 @@ extern "C" mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *
         a.tw = scratch + (size_t)s * kNoallocTwiddleStride * elem;
         a.conj = dir == 1 ? (s == 0 ? 1 : 0) | (s == M - 1 ? 2 : 0) : 0;
         a.scale = (s == M - 1 && normalize) ? 1.0 / (double)T : 1.0;
+        a.scaled = a.scale != 1.0;
         void *args[] = {&a};
         e = cudaLaunchKernel(k.fn, dim3((unsigned)pass[s].ctas), dim3(k.threads), args, k.smem, cs);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");

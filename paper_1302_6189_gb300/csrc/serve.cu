@@ -331,6 +331,7 @@ PassArgs pass_args(mdfft_server_t s, const Request *r, int pass) {
     a.tw = (const char *)p->tw + p->pass[pass].tw_offset;
     a.conj = r->dir == 1 ? (pass == 0 ? 1 : 0) | (pass == M - 1 ? 2 : 0) : 0;
     a.scale = (pass == M - 1 && r->normalize) ? 1.0 / (double)p->T : 1.0;
+    a.scaled = a.scale != 1.0;
     return a;
 }
 
@@ -464,7 +465,7 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
             Item &it = tab->items[n++];
             it.args = sp.args;
             it.args.in = a.in, it.args.out = a.out, it.args.tw = a.tw;
-            it.args.conj = a.conj, it.args.scale = a.scale;
+            it.args.conj = a.conj, it.args.scale = a.scale, it.args.scaled = a.scaled;
             it.start = total;
             it.kind = sp.kind;
             total += sp.ctas;
