@@ -75,7 +75,7 @@ def test_regimes_and_closed_forms():
     assert got["amount_slab"] == pytest.approx(oracle.amount_slab(64, 8192))
     assert got["amount_pencil"] == pytest.approx(oracle.amount_pencil(64, 8192))
     assert got["amount_volumetric"] == pytest.approx(oracle.amount_volumetric(3, 64, 8192))
-    # BASELINE labels 256^3 at P = 16, 256, 4096 as three regimes; f_3D gives 1, 1, 2
+    # the 256^3 configuration names P = 16, 256, 4096 as three regimes; f_3D gives 1, 1, 2
     for P, k in ((16, 1), (256, 1), (4096, 2), (131072, 3)):
         assert _cv((256, 256, 256), P, "abc->cab->cba")["regime"][0] == k
 
