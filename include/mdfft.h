@@ -21,13 +21,15 @@
  *    permutation of 0..M-1 (each step transforms a new axis; Sec. 3.2, the
  *    C_MD count).  Step s transforms the last axis of layout s and writes the
  *    result in layout s+1 (the "transpose" of Fig. 4); the last step writes
- *    the natural layout.
+ *    the natural layout (or keeps layout M, see MDFFT_PLAN_OUT_LAST_LAYOUT).
  *  - Every call returns an mdfft_status; nothing throws across the ABI.  On
  *    failure mdfft_last_error() returns a message for the calling thread.
  *  - Execution is asynchronous on the caller's CUDA stream.  Device memory
  *    passed in stays owned by the caller; the plan owns its own device
  *    memory (twiddles, workspace) and frees it in mdfft_destroy().
- *  - A plan may be used from one host thread at a time.
+ *  - A plan may be used from one host thread at a time.  Its executions
+ *    share the plan's workspace, so executions of one plan on different
+ *    streams must be ordered by the caller (events); on one stream they are.
  */
 #ifndef MDFFT_H
 #define MDFFT_H
