@@ -525,11 +525,47 @@ def extra_table(dev, x, P):
     res["c128"] = {"gbs": round(2 * per_transform / (ms * 1e-3) / 1e9, 1), "ms_per_transform": round(ms / B, 4),
                    "nominal_tflops_fp64": round(flops / (ms * 1e-3) / 1e12, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms]}
+    res["small_32cubed_c128"] = small_study(dev)
     res["precision_512cubed"] = precision_study(dev)
     res["md_4d_5d"] = md_study(dev)
     res["decompositions"] = decomposition_study(dev)
     res["serving"] = serving_study(dev)
     return res
+
+
+def small_study(dev, reps=2000):
+    """The 32^3 complex128 configuration (P = 4, order abc->cab->cba), forward
+    + normalised inverse per call pair: microseconds per pair with the M pass
+    launches issued one by one (mdfft_exec) and replayed from a captured
+    CUDA graph (mdfft_exec_graph)."""
+    import numpy as np
+    import torch
+
+    import synth_inputs as si
+    from paper_1302_6189_gb300 import Plan
+
+    shape = (32, 32, 32)
+    x = torch.from_numpy(si.uniform_complex(shape, si.SEEDS["parity32"], np.complex128)).to(dev)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    out = {}
+    with Plan(shape, 4, "abc->cab->cba", "c128") as pl:
+        for graph in (False, True):
+            for _ in range(20):
+                pl.exec(x, y, graph=graph)
+                pl.exec(y, z, dir=+1, normalize=True, graph=graph)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                pl.exec(x, y, graph=graph)
+                pl.exec(y, z, dir=+1, normalize=True, graph=graph)
+            b.record()
+            torch.cuda.synchronize(dev)
+            out["graph_us" if graph else "direct_us"] = round(a.elapsed_time(b) * 1e3 / reps, 2)
+        err = float((torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x)).item())
+    out["roundtrip_rel_l2"] = err
+    out["note"] = "forward + normalised inverse, 6 pass launches or 2 graph launches per pair"
+    return out
 
 
 def md_study(dev, reps=10):

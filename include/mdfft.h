@@ -156,6 +156,19 @@ mdfft_status mdfft_exec(mdfft_plan_t plan, const void *in_dev, void *out_dev, in
                         mdfft_stream_t stream);
 
 /*
+ * mdfft_exec_graph -- as mdfft_exec, replayed from a CUDA graph.  The first
+ * call for a given (in_dev, out_dev, dir, normalize) captures the plan's M
+ * pass launches into a graph (on a private stream) and instantiates it; every
+ * call then runs the graph with one cudaGraphLaunch on `stream`, which saves
+ * the per-kernel launch cost of small transforms.  A plan keeps up to 8
+ * graphs (the least recently used is replaced); mdfft_plan_autotune drops
+ * them.  Same arguments, checks and results as mdfft_exec; pass timing
+ * (mdfft_pass_timing) does not record graph executions.
+ */
+mdfft_status mdfft_exec_graph(mdfft_plan_t plan, const void *in_dev, void *out_dev, int dir, int normalize,
+                              mdfft_stream_t stream);
+
+/*
  * mdfft_exec_counted -- as mdfft_exec, and every pass also counts on the
  * device the points its store moves to another virtual process, and the
  * points exchanged for lines cut between processes.

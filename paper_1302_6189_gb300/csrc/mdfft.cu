@@ -275,6 +275,9 @@ void release(mdfft_plan_s *p) {
         if (h) cudaStreamDestroy(h);
     for (cudaEvent_t e : p->hev)
         if (e) cudaEventDestroy(e);
+    for (auto &g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (p->capture) cudaStreamDestroy(p->capture);
     delete p;
 }
 
@@ -284,7 +287,7 @@ bool overlaps(const void *a, const void *b, size_t n) {
 }
 
 mdfft_status launch_passes(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, cudaStream_t st,
-                           int64_t *counts, int64_t v);
+                           int64_t *counts, int64_t v, bool allow_timing = true);
 
 // Argument checks of an execution on device arrays (E_ARG with a message).
 mdfft_status check_exec(mdfft_plan_t p, const void *in, const void *out, int dir, int normalize, const int64_t *counts) {
@@ -324,7 +327,7 @@ mdfft_status exec_impl(mdfft_plan_t p, const void *in, void *out, int dir, int n
 // The M passes on `st`: of the whole batch (v < 0) or of transform v alone
 // (the batch axis dropped, every array offset by v T elements; no timing).
 mdfft_status launch_passes(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, cudaStream_t st,
-                           int64_t *counts, int64_t v) {
+                           int64_t *counts, int64_t v, bool allow_timing) {
     const int M = p->M;
     const bool one = v >= 0 && p->batch > 1;
     const size_t off = v >= 0 ? (size_t)v * (size_t)p->T * p->elem : 0;
@@ -337,7 +340,7 @@ mdfft_status launch_passes(mdfft_plan_t p, const void *in, void *out, int dir, i
     for (int s = M - 2; s >= 0; --s) dst[s] = (dst[s + 1] == at(out)) ? at(p->ws) : at(out);
     if (dst[0] == at(in)) dst[0] = at(p->ws2);  // in-place with an odd number of passes
     const void *src = at(in);
-    const bool timed = p->timing && v < 0;
+    const bool timed = p->timing && v < 0 && allow_timing;
     const int64_t slot = p->timed % MDFFT_TIMING_SLOTS;
     for (int s = 0; s < M; ++s) {
         Pass &ps = p->pass[s];
@@ -413,11 +416,67 @@ mdfft_status exec_host_pipelined(mdfft_plan_t p, const void *in_host, void *out_
     return MDFFT_OK;
 }
 
+// Drops the captured graphs of a plan (its launch arguments changed).
+void drop_graphs(mdfft_plan_s *p) {
+    for (auto &g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+}
+
+constexpr size_t kMaxGraphs = 8;
+
+mdfft_status exec_graph_impl(mdfft_plan_t p, const void *in, void *out, int dir, int normalize, cudaStream_t st) {
+    mdfft_status cs = check_exec(p, in, out, dir, normalize, nullptr);
+    if (cs != MDFFT_OK) return cs;
+    mdfft_plan_s::GraphEntry *hit = nullptr;
+    for (auto &g : p->graphs)
+        if (g.in == in && g.out == out && g.dir == dir && g.normalize == normalize) hit = &g;
+    if (!hit) {
+        cudaError_t e = cudaSuccess;
+        if (!p->capture) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+        e = cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        mdfft_status r = launch_passes(p, in, out, dir, normalize, p->capture, nullptr, -1, false);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(p->capture, &graph);  // ends the capture whatever happened inside
+        if (r != MDFFT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (p->graphs.size() >= kMaxGraphs) {  // replace the least recently used
+            auto lru = p->graphs.begin();
+            for (auto it = p->graphs.begin(); it != p->graphs.end(); ++it)
+                if (it->used < lru->used) lru = it;
+            cudaGraphExecDestroy(lru->exec);
+            p->graphs.erase(lru);
+        }
+        mdfft_plan_s::GraphEntry g;
+        g.in = in, g.out = out, g.dir = dir, g.normalize = normalize, g.exec = exec;
+        p->graphs.push_back(g);
+        hit = &p->graphs.back();
+    }
+    hit->used = ++p->graph_tick;
+    cudaError_t e = cudaGraphLaunch(hit->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return MDFFT_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char *mdfft_last_error(void) { return g_err.c_str(); }
+
+mdfft_status mdfft_exec_graph(mdfft_plan_t p, const void *in, void *out, int dir, int normalize,
+                              mdfft_stream_t stream) {
+    return exec_graph_impl(p, in, out, dir, normalize, reinterpret_cast<cudaStream_t>(stream));
+}
 
 int mdfft_supported_length(int64_t n, mdfft_dtype dt) {
     PassKernel k;
@@ -787,6 +846,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
     if (reps < 1) return fail(MDFFT_E_ARG, "reps must be >= 1");
     const size_t bytes = (size_t)p->T * p->batch * p->elem;
     if (overlaps(in, out, bytes)) return fail(MDFFT_E_ARG, "in and out overlap");
+    drop_graphs(p);  // captured launches would keep the old launch shapes
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

@@ -74,4 +74,15 @@ struct mdfft_plan_s {
     // (fork, copied in, computed, done)
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t hev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // mdfft_exec_graph: the passes captured per (in, out, dir, normalize), least recently used replaced
+    struct GraphEntry {
+        const void *in = nullptr;
+        void *out = nullptr;
+        int dir = 0, normalize = 0;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_tick = 0;
+    cudaStream_t capture = nullptr;  // private stream the passes are captured on
 };

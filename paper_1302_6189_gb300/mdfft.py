@@ -59,6 +59,7 @@ SIGNATURES = {
     "mdfft_plan": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint]),
     "mdfft_plan_batched": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint, i64]),
     "mdfft_exec": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "mdfft_exec_graph": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_exec_counted": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "mdfft_comm_volume": (c_int, [c_void_p, P_(MdfftComm)]),
     "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
@@ -167,6 +168,11 @@ def mdfft_plan_batched(N, P, order=None, dtype=MDFFT_C64, flags=0, batch=1):
 def mdfft_exec(plan, in_ptr, out_ptr, dir=-1, normalize=0, stream=0):
     _check(_lib.mdfft_exec(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(dir), int(normalize),
                            c_void_p(stream)), "mdfft_exec")
+
+
+def mdfft_exec_graph(plan, in_ptr, out_ptr, dir=-1, normalize=0, stream=0):
+    _check(_lib.mdfft_exec_graph(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(dir), int(normalize),
+                                 c_void_p(stream)), "mdfft_exec_graph")
 
 
 def mdfft_exec_counted(plan, in_ptr, out_ptr, dir, normalize, stream, counts_ptr):
@@ -412,10 +418,12 @@ class Plan:
         self._check_tensor(out, "out", self.out_shape)
         return out
 
-    def exec(self, x, out=None, dir=-1, normalize=False, stream=None):
+    def exec(self, x, out=None, dir=-1, normalize=False, stream=None, graph=False):
+        """graph=True replays the passes from a CUDA graph captured for these arrays (mdfft_exec_graph)."""
         self._check_tensor(x, "input")
         out = self._out(x, out)
-        mdfft_exec(self.handle, x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
+        run = mdfft_exec_graph if graph else mdfft_exec
+        run(self.handle, x.data_ptr(), out.data_ptr(), dir, int(bool(normalize)), self._stream(stream))
         return out
 
     def exec_counted(self, x, out=None, dir=-1, normalize=False, stream=None):
