@@ -193,6 +193,21 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
         a.nrest++;
         ps.ctas *= p->batch;
     }
+    // small grids: shrink the tile (along h first, then along g down to
+    // 128-byte store runs) until the pass fills about one resident wave of
+    // CTAs; idle lanes in a CTA cost less than idle SMs
+    const int64_t rest = ps.ctas / (a.gblocks * a.hblocks);
+    const int64_t wave = mdfft::detail::wave_ctas(ps.k);
+    const int min_bg = std::max(1, (int)(128 / p->elem));
+    while (ps.ctas < wave && (a.Bh > 1 || (!line_store && a.Bg > min_bg))) {
+        if (a.Bh > 1)
+            a.Bh = (a.Bh + 1) / 2;
+        else
+            a.Bg = std::max(min_bg, (a.Bg + 1) / 2);
+        a.gblocks = (Ng + a.Bg - 1) / a.Bg;
+        a.hblocks = (Nh + a.Bh - 1) / a.Bh;
+        ps.ctas = a.gblocks * a.hblocks * rest;
+    }
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
