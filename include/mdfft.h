@@ -169,6 +169,18 @@ mdfft_status mdfft_exec_graph(mdfft_plan_t plan, const void *in_dev, void *out_d
                               mdfft_stream_t stream);
 
 /*
+ * mdfft_selftest_wait -- runs, alone in one thread, the bounded mbarrier wait
+ * the persistent pipelined kernels use for their bulk copies: arrive = 0
+ * arms the barrier for 16 bytes that no copy brings, so the wait must give up
+ * after limit_us microseconds (1 .. 10^7) and the call returns
+ * MDFFT_E_TIMEOUT with the device still usable; arrive = 1 completes the phase
+ * with a plain arrival and returns MDFFT_OK at once.  *waited_us (may be NULL)
+ * receives the host-measured duration.  Synchronous; allocates 4 bytes of
+ * device memory for the status.  (Failure detection without a fault.)
+ */
+mdfft_status mdfft_selftest_wait(int arrive, int64_t limit_us, int64_t *waited_us);
+
+/*
  * mdfft_exec_counted -- as mdfft_exec, and every pass also counts on the
  * device the points its store moves to another virtual process, and the
  * points exchanged for lines cut between processes.

@@ -60,6 +60,7 @@ SIGNATURES = {
     "mdfft_plan_batched": (c_int, [P_(c_void_p), c_int, P_(i64), i64, P_(c_int), c_int, ctypes.c_uint, i64]),
     "mdfft_exec": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_exec_graph": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "mdfft_selftest_wait": (c_int, [c_int, i64, P_(i64)]),
     "mdfft_exec_counted": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "mdfft_comm_volume": (c_int, [c_void_p, P_(MdfftComm)]),
     "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
@@ -173,6 +174,13 @@ def mdfft_exec(plan, in_ptr, out_ptr, dir=-1, normalize=0, stream=0):
 def mdfft_exec_graph(plan, in_ptr, out_ptr, dir=-1, normalize=0, stream=0):
     _check(_lib.mdfft_exec_graph(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(dir), int(normalize),
                                  c_void_p(stream)), "mdfft_exec_graph")
+
+
+def mdfft_selftest_wait(arrive, limit_us):
+    """Returns (status, microseconds waited); status MDFFT_E_TIMEOUT when the wait gave up."""
+    waited = i64()
+    st = _lib.mdfft_selftest_wait(int(arrive), int(limit_us), ctypes.byref(waited))
+    return st, waited.value
 
 
 def mdfft_exec_counted(plan, in_ptr, out_ptr, dir, normalize, stream, counts_ptr):

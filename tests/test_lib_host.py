@@ -299,3 +299,9 @@ def test_output_in_the_last_layout_moves_nothing_at_the_end():
             md.mdfft_destroy(h)
         ref = oracle.comm_volume((8, 6, 4), 6, order)
         assert cv["final_to_natural"] == 0 and cv["per_transition"] == ref["per_transition"]
+
+
+def test_wait_selftest_arguments():
+    for bad in (0, -5, 10_000_001):
+        st, _ = md.mdfft_selftest_wait(0, bad)
+        assert st == md.mdfft.MDFFT_E_ARG
