@@ -377,6 +377,7 @@ typedef struct {
     int64_t inflight, queued;
     size_t bytes_in_use, budget_bytes;
     int grid_ctas; /* CTAs of the persistent kernel */
+    int64_t cancelled;
 } mdfft_server_stats;
 
 /* budget_bytes: HBM admission budget; max_inflight: 1..512 requests in
@@ -397,8 +398,15 @@ mdfft_status mdfft_server_run(mdfft_server_t s, int max_steps, int *steps);
  * is then its completion time on the server clock, in ms since the last
  * mdfft_server_reset_clock (or creation), taken from CUDA events. */
 mdfft_status mdfft_server_poll(mdfft_server_t s, int64_t request_id, int *done, double *done_ms);
-/* Forget a finished request. */
+/* Forget a finished (or cancelled) request. */
 mdfft_status mdfft_server_release(mdfft_server_t s, int64_t request_id);
+/* Cancels a request: a queued one is dropped before it reaches the GPU; an
+ * admitted one gets no further passes and its budget and workspace come back
+ * once its latest step has run (its out_dev then holds partial results).  A
+ * request whose last pass is already on the GPU completes normally.  A
+ * cancelled request polls as done with done_ms = -1.  E_ARG for unknown,
+ * finished or already cancelled requests. */
+mdfft_status mdfft_server_cancel(mdfft_server_t s, int64_t request_id);
 /* Steps until every submitted request is done (blocks the host). */
 mdfft_status mdfft_server_drain(mdfft_server_t s);
 /* Sets the server clock's zero to now (records an event on the stream and waits for it). */

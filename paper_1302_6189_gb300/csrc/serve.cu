@@ -193,6 +193,8 @@ struct Request {
     bool admitted = false, finished = false;
     double done_ms = -1.0;  // completion on the server clock
     int slot = -1;          // slot of the step that ran the last pass
+    int last_slot = -1;     // slot of the latest step that ran one of its passes
+    bool cancelled = false;
 };
 
 struct Slot {
@@ -272,11 +274,11 @@ void resolve_slot(mdfft_server_t s, Slot &sl) {
     cudaEventElapsedTime(&ms, s->t0, sl.done);
     for (Request *r : sl.finishing) {
         r->finished = true;
-        r->done_ms = ms;
+        r->done_ms = r->cancelled ? -1.0 : ms;
         if (r->has_ws) s->arena.release(r->ws_off, (size_t)r->plan->T * r->plan->elem);
         r->has_ws = false;
         s->in_use -= r->bytes;
-        s->stats.completed++;
+        (r->cancelled ? s->stats.cancelled : s->stats.completed)++;
         s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), r));
     }
     sl.finishing.clear();
@@ -471,6 +473,7 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
             total += sp.ctas;
         }
         r->next_pass++;
+        r->last_slot = s->next_slot;
         if (r->next_pass == r->plan->M) {
             r->slot = s->next_slot;
             sl.finishing.push_back(r);
@@ -541,6 +544,38 @@ mdfft_status mdfft_server_release(mdfft_server_t s, int64_t request_id) {
     if (!it->second->finished) return fail(MDFFT_E_ARG, "request not finished");
     delete it->second;
     s->requests.erase(it);
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_cancel(mdfft_server_t s, int64_t request_id) {
+    if (!s) return fail(MDFFT_E_ARG, "null server");
+    auto it = s->requests.find(request_id);
+    if (it == s->requests.end()) return fail(MDFFT_E_ARG, "unknown request id");
+    Request *r = it->second;
+    if (r->finished || r->cancelled) return fail(MDFFT_E_ARG, "request already finished or cancelled");
+    if (!r->admitted) {  // still queued: it never reached the GPU
+        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+        r->cancelled = r->finished = true;
+        r->done_ms = -1.0;
+        s->stats.cancelled++;
+        return MDFFT_OK;
+    }
+    if (r->next_pass == r->plan->M) return MDFFT_OK;  // its last pass is on the GPU: it completes
+    r->cancelled = true;
+    r->next_pass = r->plan->M;  // no further passes are scheduled
+    Slot *last = r->last_slot >= 0 ? &s->slots[r->last_slot] : nullptr;
+    if (last && last->busy) {  // resources come back when its latest step has run
+        r->slot = r->last_slot;
+        last->finishing.push_back(r);
+    } else {  // nothing of it is on the GPU
+        r->finished = true;
+        r->done_ms = -1.0;
+        if (r->has_ws) s->arena.release(r->ws_off, (size_t)r->plan->T * r->plan->elem);
+        r->has_ws = false;
+        s->in_use -= r->bytes;
+        s->stats.cancelled++;
+        s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), r));
+    }
     return MDFFT_OK;
 }
 

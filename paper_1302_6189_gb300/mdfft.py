@@ -52,7 +52,8 @@ class MdfftPassInfo(ctypes.Structure):
 class MdfftServerStats(ctypes.Structure):
     _fields_ = [("submitted", i64), ("admitted", i64), ("completed", i64), ("steps", i64),
                 ("graph_launches", i64), ("kernel_launches", i64), ("inflight", i64), ("queued", i64),
-                ("bytes_in_use", c_size_t), ("budget_bytes", c_size_t), ("grid_ctas", c_int)]
+                ("bytes_in_use", c_size_t), ("budget_bytes", c_size_t), ("grid_ctas", c_int),
+                ("cancelled", i64)]
 
 
 SIGNATURES = {
@@ -89,6 +90,7 @@ SIGNATURES = {
     "mdfft_server_run": (c_int, [c_void_p, c_int, P_(c_int)]),
     "mdfft_server_poll": (c_int, [c_void_p, i64, P_(c_int), P_(ctypes.c_double)]),
     "mdfft_server_release": (c_int, [c_void_p, i64]),
+    "mdfft_server_cancel": (c_int, [c_void_p, i64]),
     "mdfft_server_drain": (c_int, [c_void_p]),
     "mdfft_server_reset_clock": (c_int, [c_void_p]),
     "mdfft_server_set_grid": (c_int, [c_void_p, c_int]),
@@ -351,6 +353,10 @@ def mdfft_server_release(server, request_id):
     _check(_lib.mdfft_server_release(server, int(request_id)), "mdfft_server_release")
 
 
+def mdfft_server_cancel(server, request_id):
+    _check(_lib.mdfft_server_cancel(server, int(request_id)), "mdfft_server_cancel")
+
+
 def mdfft_server_drain(server):
     _check(_lib.mdfft_server_drain(server), "mdfft_server_drain")
 
@@ -550,6 +556,9 @@ class Server:
 
     def release(self, rid):
         mdfft_server_release(self.handle, rid)
+
+    def cancel(self, rid):
+        mdfft_server_cancel(self.handle, rid)
 
     def drain(self):
         mdfft_server_drain(self.handle)

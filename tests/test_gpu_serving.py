@@ -114,3 +114,38 @@ def test_single_cta_grid_and_errors():
         with pytest.raises(md.MdfftError):
             srv.poll(12345)
     assert torch.equal(y, alone(shape, x, -1, False))
+
+
+def test_cancel_queued_and_in_flight_requests():
+    # budget for two 64^3 requests: the third waits in the queue and is
+    # cancelled there; the first is cancelled after its first pass was
+    # launched; the others finish exactly as alone, and the budget comes back
+    shape = (64, 64, 64)
+    bytes_req = 3 * 64 ** 3 * 8
+    xs = [torch.from_numpy(si.uniform_complex(shape, 650 + i, np.complex64)).to(DEV) for i in range(4)]
+    outs = [torch.empty_like(x) for x in xs]
+    with md.Server(budget_bytes=2 * bytes_req + 4096, max_inflight=8) as srv:
+        srv.set_depth(1)
+        ids = [srv.submit(x, y) for x, y in zip(xs, outs)]
+        srv.step()  # admits requests 0 and 1, launches their first pass
+        st = srv.stats()
+        assert st["inflight"] == 2 and st["queued"] == 2
+        srv.cancel(ids[2])  # still queued
+        srv.cancel(ids[0])  # in flight: no further passes
+        with pytest.raises(md.MdfftError):
+            srv.cancel(ids[2])  # already cancelled
+        srv.drain()
+        st = srv.stats()
+        assert st["cancelled"] == 2 and st["completed"] == 2
+        assert st["bytes_in_use"] == 0 and st["inflight"] == 0 and st["queued"] == 0
+        for i in (0, 2):
+            done, ms = srv.poll(ids[i])
+            assert done and ms == -1.0
+            srv.release(ids[i])
+        for i in (1, 3):
+            done, ms = srv.poll(ids[i])
+            assert done and ms >= 0
+            with pytest.raises(md.MdfftError):
+                srv.cancel(ids[i])  # finished
+    for i in (1, 3):
+        assert torch.equal(outs[i], alone(shape, xs[i], -1, False))
