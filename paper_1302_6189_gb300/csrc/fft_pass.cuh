@@ -205,33 +205,32 @@ __host__ __device__ constexpr double cos16(int k) {
 }
 __host__ __device__ constexpr double sin16(int k) { return cos16(k <= 4 ? 4 - k : k - 4); }  // sin(k pi/8) = cos((4-k) pi/8)
 
-// x * w_16^K for a compile-time K in [0, 8)
-template <int K, typename C> __device__ __forceinline__ C rot16(C x) {
-    using R = decltype(x.x);
+// e +- o w_16^K in six multiply-adds for the angles that need a product:
+// o w = (o.x c + o.y s, o.y c - o.x s) (c, s = cos, sin of 2 pi K/16) is
+// written f (u.x, u.y) with the larger of |c|, |s| factored out as f, so
+// that u needs one multiply-add per part with a factor of magnitude <= 1;
+// then e + f u and e - f u are one multiply-add per part each.
+template <int K, typename C> __device__ __forceinline__ void butterfly16(C &lo, C &hi, const C &e, const C &o) {
+    using R = decltype(o.x);
     if constexpr (K == 0) {
-        return x;
-    } else if constexpr (K == 4) {  // -i
-        return {x.y, -x.x};
-    } else if constexpr (K == 2) {  // (1 - i)/sqrt(2)
-        const R h = (R)0.70710678118654752440;
-        return {(x.x + x.y) * h, (x.y - x.x) * h};
-    } else if constexpr (K == 6) {  // (-1 - i)/sqrt(2)
-        const R h = (R)0.70710678118654752440;
-        return {(x.y - x.x) * h, -(x.x + x.y) * h};
+        lo = cadd(e, o), hi = csub(e, o);
+    } else if constexpr (K == 4) {  // o (-i)
+        lo = C{e.x + o.y, e.y - o.x}, hi = C{e.x - o.y, e.y + o.x};
     } else {
-        const R c = (R)cos16(K), s = (R)sin16(K);
-        return {x.x * c + x.y * s, x.y * c - x.x * s};
+        constexpr double c = cos16(K), s = sin16(K);
+        constexpr bool by_c = (c < 0 ? -c : c) >= (s < 0 ? -s : s);
+        constexpr R f = (R)(by_c ? c : s), t = (R)(by_c ? s / c : c / s);
+        const C u = by_c ? C{o.x + t * o.y, o.y - t * o.x} : C{o.y + t * o.x, t * o.y - o.x};
+        lo = C{e.x + f * u.x, e.y + f * u.y};
+        hi = C{e.x - f * u.x, e.y - f * u.y};
     }
 }
 
-// radix-2 decimation in time: v = DFT_R(v), R a power of two <= 16
 template <int R, typename C> struct DftPow2 {
     template <int K> __device__ __forceinline__ static void combine(C (&v)[R], const C (&e)[R / 2],
                                                                     const C (&o)[R / 2]) {
         if constexpr (K < R / 2) {
-            C t = rot16<K * (16 / R)>(o[K]);
-            v[K] = cadd(e[K], t);
-            v[K + R / 2] = csub(e[K], t);
+            butterfly16<K * (16 / R)>(v[K], v[K + R / 2], e[K], o[K]);
             combine<K + 1>(v, e, o);
         }
     }
