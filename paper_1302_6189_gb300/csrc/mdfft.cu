@@ -208,6 +208,7 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
         a.hblocks = (Nh + a.Bh - 1) / a.Bh;
         ps.ctas = a.gblocks * a.hblocks * rest;
     }
+    a.tile32 = ps.ctas <= 0xffffffffLL;
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
@@ -240,6 +241,7 @@ void mdfft::detail::retile_pass(const mdfft_plan_s *p, int s, int lines, PassArg
     a.hblocks = (a.Nh + Bh - 1) / Bh;
     int64_t n = a.gblocks * a.hblocks;
     for (int i = 0; i < a.nrest; ++i) n *= a.rest_count[i];
+    a.tile32 = n <= 0xffffffffLL;
     *out = a;
     *ctas = n;
 }
@@ -908,6 +910,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 a.hblocks = (a.Nh + a.Bh - 1) / a.Bh;
                 cand.ctas = a.gblocks * a.hblocks;
                 for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
+                a.tile32 = cand.ctas <= 0xffffffffLL;
                 cand.grid = kv.persistent ? std::min<int64_t>(cand.ctas, mdfft::detail::wave_ctas(kv)) : cand.ctas;
                 a.in = in;
                 a.out = out;
@@ -1124,6 +1127,7 @@ mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dt
         a.nrest++;
         ps.ctas *= N[ax];
     }
+    a.tile32 = ps.ctas <= 0xffffffffLL;
     a.scale = 1.0;
     a.scaled = 0;
     return MDFFT_OK;
