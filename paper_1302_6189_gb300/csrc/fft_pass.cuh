@@ -48,6 +48,20 @@ struct OwnerMap {
     int64_t line_div;
 };
 
+// Division of a 32-bit n by a divisor d fixed for the launch, as a
+// multiply-high and a shift (Granlund and Montgomery, division by invariant
+// integers using multiplication: with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, floor(n / d) = (mulhi(m, n) + n) >> l,
+// the sum taken in 64 bits).  The host fills m and l (fastdiv_make).
+struct FastDiv {
+    uint32_t d, m, l;
+};
+__host__ __device__ constexpr FastDiv fastdiv_make(uint32_t d) {
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    return FastDiv{d, (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1), l};
+}
+
 struct PassArgs {
     const void *in;
     void *out;
@@ -68,6 +82,7 @@ struct PassArgs {
     int scaled;                     // scale != 1 (set with scale, so the kernel tests an integer, not a double)
     int64_t ntiles;                 // tiles of the pass (persistent kernels walk them)
     int tile32;                     // every tile index and tile count fits 32 bits (cheaper divisions)
+    FastDiv fd_g, fd_h, fd_rest[kMaxTileDims];  // gblocks, hblocks, rest_count as multiply-shift divisors
     int *err;                       // persistent kernels: set to 1 if a bounded wait gave up (may be null)
     unsigned long long *moved;      // count mode: points whose owner changes (null: off)
     unsigned long long *split;      // count mode: split-line amount of the input layout
@@ -421,20 +436,27 @@ struct TileCoord {
 // Tile index -> coordinates, g fastest.  With tile32 (the host checked that
 // the pass has fewer than 2^32 tiles, so every count and quotient fits) the
 // divisions run in 32 bits, several times cheaper than in 64.
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv &f) {
+    return (uint32_t)(((uint64_t)__umulhi(n, f.m) + n) >> f.l);
+}
+
 __device__ __forceinline__ TileCoord tile_coords32(const PassArgs &a, uint32_t t) {
     TileCoord c;
-    const uint32_t gb = t % (uint32_t)a.gblocks;
-    t /= (uint32_t)a.gblocks;
-    const uint32_t hb = t % (uint32_t)a.hblocks;
-    t /= (uint32_t)a.hblocks;
+    uint32_t q = fastdiv(t, a.fd_g);
+    const uint32_t gb = t - q * a.fd_g.d;
+    t = q;
+    q = fastdiv(t, a.fd_h);
+    const uint32_t hb = t - q * a.fd_h.d;
+    t = q;
     c.g0 = (int64_t)gb * a.Bg, c.h0 = (int64_t)hb * a.Bh;
     c.in_base = c.g0 * a.in_sg + c.h0 * a.in_sh;
     c.out_base = c.g0 * a.out_sg + c.h0 * a.out_sh;
     for (int i = 0; i < a.nrest; ++i) {
-        const uint32_t q = t % (uint32_t)a.rest_count[i];
-        t /= (uint32_t)a.rest_count[i];
-        c.in_base += (int64_t)q * a.rest_in[i];
-        c.out_base += (int64_t)q * a.rest_out[i];
+        q = fastdiv(t, a.fd_rest[i]);
+        const uint32_t r = t - q * a.fd_rest[i].d;
+        t = q;
+        c.in_base += (int64_t)r * a.rest_in[i];
+        c.out_base += (int64_t)r * a.rest_out[i];
     }
     return c;
 }

@@ -57,6 +57,15 @@ void layout_strides(const pl::Layout &L, const int64_t *N, int64_t *stride) {
     }
 }
 
+// tile32 and the multiply-shift divisors of the tile decomposition (after any change of the tiling)
+void set_tile_divisors(PassArgs &a, int64_t ctas) {
+    a.tile32 = ctas <= 0xffffffffLL;
+    if (!a.tile32) return;
+    a.fd_g = mdfft::fastdiv_make((uint32_t)a.gblocks);
+    a.fd_h = mdfft::fastdiv_make((uint32_t)a.hblocks);
+    for (int i = 0; i < a.nrest; ++i) a.fd_rest[i] = mdfft::fastdiv_make((uint32_t)a.rest_count[i]);
+}
+
 mdfft::OwnerMap owner_map(int M, const int64_t *N, int64_t P, const pl::Layout &L) {
     int64_t d[pl::kMaxDims];
     pl::layout_dims(L, N, d);
@@ -208,7 +217,7 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
         a.hblocks = (Nh + a.Bh - 1) / a.Bh;
         ps.ctas = a.gblocks * a.hblocks * rest;
     }
-    a.tile32 = ps.ctas <= 0xffffffffLL;
+    set_tile_divisors(a, ps.ctas);
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
@@ -241,7 +250,7 @@ void mdfft::detail::retile_pass(const mdfft_plan_s *p, int s, int lines, PassArg
     a.hblocks = (a.Nh + Bh - 1) / Bh;
     int64_t n = a.gblocks * a.hblocks;
     for (int i = 0; i < a.nrest; ++i) n *= a.rest_count[i];
-    a.tile32 = n <= 0xffffffffLL;
+    set_tile_divisors(a, n);
     *out = a;
     *ctas = n;
 }
@@ -910,7 +919,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 a.hblocks = (a.Nh + a.Bh - 1) / a.Bh;
                 cand.ctas = a.gblocks * a.hblocks;
                 for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
-                a.tile32 = cand.ctas <= 0xffffffffLL;
+                set_tile_divisors(a, cand.ctas);
                 cand.grid = kv.persistent ? std::min<int64_t>(cand.ctas, mdfft::detail::wave_ctas(kv)) : cand.ctas;
                 a.in = in;
                 a.out = out;
@@ -1127,7 +1136,7 @@ mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dt
         a.nrest++;
         ps.ctas *= N[ax];
     }
-    a.tile32 = ps.ctas <= 0xffffffffLL;
+    set_tile_divisors(a, ps.ctas);
     a.scale = 1.0;
     a.scaled = 0;
     return MDFFT_OK;
