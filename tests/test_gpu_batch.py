@@ -112,3 +112,44 @@ def test_pipelined_host_execution(shape, P, B):
         assert torch.equal(hz, back.cpu())
     for i in range(B):
         assert _rel(hz[i].numpy(), vols[i]) < TOL["c64"]
+
+
+def test_last_layout_output_through_host_pipeline_and_graph():
+    # MDFFT_PLAN_OUT_LAST_LAYOUT with a batch: the pipelined host path and the
+    # graph replay give the device call's bytes
+    shape, P, B = (24, 32, 20), 12, 3
+    x = torch.from_numpy(np.stack(_volumes(shape, B, "c64", 560))).to(DEV)
+    with md.Plan(shape, P, None, "c64", md.MDFFT_PLAN_OUT_LAST_LAYOUT, batch=B) as pl:
+        want = pl.exec(x)
+        assert tuple(want.shape) == pl.out_shape
+        hx = x.cpu().pin_memory()
+        hy = torch.empty(pl.out_shape, dtype=torch.complex64).pin_memory()
+        din = torch.empty_like(x)
+        dout = torch.empty(pl.out_shape, dtype=torch.complex64, device=DEV)
+        pl.exec_host(hx, hy, din, dout)
+        g = torch.empty_like(want)
+        pl.exec(x, g, graph=True)
+        torch.cuda.synchronize()
+        assert torch.equal(hy, want.cpu())
+        assert torch.equal(g, want)
+        last = pl.order()[-1]
+    for i in range(B):
+        ref = np.transpose(oracle.fftn(x[i].cpu().numpy().astype(np.complex128)), last)
+        assert _rel(want[i].cpu().numpy(), ref) < TOL["c64"]
+
+
+@pytest.mark.parametrize("shape,P,B", [((8, 6, 10, 4), 16, 3), ((6, 4, 5, 4, 3), 20, 2)])
+def test_batched_higher_dims_graph_and_counts(shape, P, B):
+    M = len(shape)
+    x = torch.from_numpy(np.stack(_volumes(shape, B, "c128", 570))).to(DEV)
+    with md.Plan(shape, P, None, "c128", batch=B) as pl:
+        want = pl.exec(x)
+        assert torch.equal(pl.exec(x, graph=True), want)
+        _, counts = pl.exec_counted(x)
+        c = counts.cpu().tolist()
+        order = pl.order()
+    ref = oracle.comm_volume(shape, P, order)
+    assert c[: M - 1] == [B * v for v in ref["per_transition"]]
+    for i in range(B):
+        r = oracle.fftn(x[i].cpu().numpy())
+        assert _rel(want[i].cpu().numpy(), r) < TOL["c128"]
