@@ -428,7 +428,7 @@ def run_ours(args):
     link["frac_of_concurrent"] = round(host_bytes / (e_ms / e_steps * 1e-3) / 1e9 / link["concurrent_gbs"], 3)
 
     extra = None
-    if not args.no_extra:
+    if not args.no_extra and world == 1:  # single-GPU studies: not repeated on every rank of a replica run
         extra = extra_table(dev, xs, P)
 
     if rank != 0:
