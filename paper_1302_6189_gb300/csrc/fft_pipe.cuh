@@ -121,10 +121,10 @@ __global__ void __launch_bounds__(PassCfg<float, N, 0, 0>::THREADS) fft_pass_pip
     using Cfg = PassCfg<float, N, 0, 0>;
     using P = PipeCfg<N, NBUF>;
     using C = float2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-    C *land = reinterpret_cast<C *>(smem_raw + P::HEAD);
-    unsigned char *work = smem_raw + P::HEAD + NBUF * (size_t)P::LAND * sizeof(C);
+    extern __shared__ __align__(128) unsigned char pipe_smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(pipe_smem);
+    C *land = reinterpret_cast<C *>(pipe_smem + P::HEAD);
+    unsigned char *work = pipe_smem + P::HEAD + NBUF * (size_t)P::LAND * sizeof(C);
     C *buf = reinterpret_cast<C *>(work);
     C *tw = buf + Cfg::DATA;
     int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);

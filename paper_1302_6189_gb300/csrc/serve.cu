@@ -39,7 +39,10 @@ constexpr int kThreads = 256;   // CTA size of the persistent kernel (every leng
 // line lengths the persistent kernel carries (complex64); other lengths run
 // as separate launches of their own pass kernel within the same step
 #define MDFFT_SERVE_LENGTHS(X) X(0, 16) X(1, 24) X(2, 32) X(3, 48) X(4, 64) X(5, 96) X(6, 128) X(7, 160) X(8, 192) X(9, 256)
-constexpr int kKinds = 10;
+#define MDFFT_COUNT_KIND(i, N) +1
+constexpr int kKinds = 0 MDFFT_SERVE_LENGTHS(MDFFT_COUNT_KIND);
+#undef MDFFT_COUNT_KIND
+static_assert(kKinds == 10, "serving kinds are numbered 0 .. kKinds - 1 in MDFFT_SERVE_LENGTHS");
 
 struct Item {
     PassArgs args;
