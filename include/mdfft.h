@@ -315,6 +315,20 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * ms_before / ms_after (M entries each, may be NULL) receive the mean pass
  * times of the default and of the chosen configuration.
  */
+/*
+ * mdfft_plan_tuning / mdfft_plan_set_tuning -- a plan's launch choices as 4
+ * int32 per pass (kernel variant: 0 default, 1 fixed 256-thread CTAs, 2
+ * fixed 512-thread CTAs, 3 / 4 persistent pipelined with 1 / 2 landing
+ * buffers; lines per tile along g; lines per tile along h; 0), e.g. after
+ * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,
+ * order, dtype, batch and flags.  set_tuning checks every pass (variant built
+ * for its length and dtype, tile within the kernel's lines and the pass's
+ * extents) before changing any; it drops captured graphs.  Results do not
+ * depend on the tuning.  cap / n: 4 M.  Host-only plans: E_ARG.
+ */
+mdfft_status mdfft_plan_tuning(mdfft_plan_t plan, int32_t *out, int cap);
+mdfft_status mdfft_plan_set_tuning(mdfft_plan_t plan, const int32_t *in, int n);
+
 mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *out_dev, int reps, mdfft_stream_t stream,
                                  float *ms_before, float *ms_after);
 

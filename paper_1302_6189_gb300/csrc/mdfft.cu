@@ -959,6 +959,78 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
     return result;
 }
 
+namespace {
+
+// The launch variants the autotuner chooses among, by code:
+// 0 default, 1 / 2 fixed 256 / 512-thread CTAs, 3 / 4 pipelined with 1 / 2 landing buffers.
+bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
+    const int64_t n = p->pass[s].n;
+    switch (variant) {
+        case 0:
+            return lookup(p->dt, n, k);
+        case 1:
+        case 2:
+            return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_thr(n, variant == 1 ? 256 : 512, k);
+        case 3:
+        case 4:
+            return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_pipe(n, variant - 2, k);
+        default:
+            return false;
+    }
+}
+
+}  // namespace
+
+mdfft_status mdfft_plan_tuning(mdfft_plan_t p, int32_t *out, int cap) {
+    if (!p || !out) return fail(MDFFT_E_ARG, "null argument");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan has no passes");
+    if (cap < 4 * p->M) return fail(MDFFT_E_ARG, "cap must be at least 4 M");
+    for (int s = 0; s < p->M; ++s) {
+        const Pass &ps = p->pass[s];
+        int variant = -1;
+        for (int v = 0; v <= 4 && variant < 0; ++v) {
+            PassKernel k;
+            if (tuning_kernel(p, s, v, &k) && k.fn == ps.k.fn) variant = v;
+        }
+        if (variant < 0) return fail(MDFFT_E_CUDA, "internal: unknown pass kernel");
+        out[4 * s] = variant, out[4 * s + 1] = ps.args.Bg, out[4 * s + 2] = ps.args.Bh, out[4 * s + 3] = 0;
+    }
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_plan_set_tuning(mdfft_plan_t p, const int32_t *in, int n) {
+    if (!p || !in) return fail(MDFFT_E_ARG, "null argument");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan has no passes");
+    if (n != 4 * p->M) return fail(MDFFT_E_ARG, "expected 4 M entries");
+    Pass next[MDFFT_MAX_DIMS];
+    for (int s = 0; s < p->M; ++s) {  // validate everything before changing anything
+        Pass cand = p->pass[s];
+        PassKernel k;
+        const int variant = in[4 * s], Bg = in[4 * s + 1], Bh = in[4 * s + 2];
+        if (!tuning_kernel(p, s, variant, &k)) return fail(MDFFT_E_ARG, "kernel variant not built for this pass");
+        if (k.persistent && k.lines != p->pass[s].k.lines)
+            return fail(MDFFT_E_ARG, "pipelined variant needs the default tile lines");
+        PassArgs &a = cand.args;
+        if (Bg < 1 || Bh < 1 || (int64_t)Bg * Bh > k.lines || Bg > a.Ng || Bh > a.Nh)
+            return fail(MDFFT_E_ARG, "tile shape does not fit the kernel or the pass");
+        if (k.smem > 48 * 1024 &&
+            cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
+            return fail(MDFFT_E_CUDA, "cudaFuncSetAttribute");
+        cand.k = k;
+        a.Bg = Bg, a.Bh = Bh;
+        a.gblocks = (a.Ng + Bg - 1) / Bg;
+        a.hblocks = (a.Nh + Bh - 1) / Bh;
+        cand.ctas = a.gblocks * a.hblocks;
+        for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
+        cand.grid = k.persistent ? std::min<int64_t>(cand.ctas, mdfft::detail::wave_ctas(k)) : cand.ctas;
+        set_tile_divisors(a, cand.ctas);
+        next[s] = cand;
+    }
+    for (int s = 0; s < p->M; ++s) p->pass[s] = next[s];
+    drop_graphs(p);
+    return MDFFT_OK;
+}
+
 mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {
     if (!p || !out) return fail(MDFFT_E_ARG, "null argument");
     if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan has no passes");

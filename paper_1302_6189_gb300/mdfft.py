@@ -62,6 +62,8 @@ SIGNATURES = {
     "mdfft_exec": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_exec_graph": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "mdfft_selftest_wait": (c_int, [c_int, i64, P_(i64)]),
+    "mdfft_plan_tuning": (c_int, [c_void_p, P_(ctypes.c_int32), c_int]),
+    "mdfft_plan_set_tuning": (c_int, [c_void_p, P_(ctypes.c_int32), c_int]),
     "mdfft_exec_counted": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "mdfft_comm_volume": (c_int, [c_void_p, P_(MdfftComm)]),
     "mdfft_chunk": (c_int, [c_void_p, c_int, i64, P_(i64), P_(i64), P_(i64), P_(i64)]),
@@ -183,6 +185,25 @@ def mdfft_selftest_wait(arrive, limit_us):
     waited = i64()
     st = _lib.mdfft_selftest_wait(int(arrive), int(limit_us), ctypes.byref(waited))
     return st, waited.value
+
+
+TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2")
+
+
+def mdfft_plan_tuning(plan, M):
+    """[{"variant": ..., "tile_g": ..., "tile_h": ...} per pass] (JSON-friendly)."""
+    arr = (ctypes.c_int32 * (4 * M))()
+    _check(_lib.mdfft_plan_tuning(plan, arr, 4 * M), "mdfft_plan_tuning")
+    return [{"variant": TUNING_VARIANTS[arr[4 * s]], "tile_g": arr[4 * s + 1], "tile_h": arr[4 * s + 2]}
+            for s in range(M)]
+
+
+def mdfft_plan_set_tuning(plan, tuning):
+    vals = []
+    for t in tuning:
+        vals += [TUNING_VARIANTS.index(t["variant"]), int(t["tile_g"]), int(t["tile_h"]), 0]
+    arr = (ctypes.c_int32 * len(vals))(*vals)
+    _check(_lib.mdfft_plan_set_tuning(plan, arr, len(vals)), "mdfft_plan_set_tuning")
 
 
 def mdfft_exec_counted(plan, in_ptr, out_ptr, dir, normalize, stream, counts_ptr):
@@ -498,6 +519,14 @@ class Plan:
         self._check_tensor(x, "input")
         self._check_tensor(scratch, "scratch", self.out_shape)
         return mdfft_pattern_probe(self.handle, s, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream))
+
+    def tuning(self):
+        """The launch choices of every pass (store them, e.g. as JSON, after autotune)."""
+        return mdfft_plan_tuning(self.handle, self.M)
+
+    def set_tuning(self, tuning):
+        """Reapply stored launch choices (same dims, P, order, dtype, batch and flags)."""
+        mdfft_plan_set_tuning(self.handle, tuning)
 
     def check(self):
         """Raises MdfftError (E_TIMEOUT) if a device-side bounded wait gave up."""

@@ -305,3 +305,12 @@ def test_wait_selftest_arguments():
     for bad in (0, -5, 10_000_001):
         st, _ = md.mdfft_selftest_wait(0, bad)
         assert st == md.mdfft.MDFFT_E_ARG
+
+
+def test_tuning_needs_device_plans():
+    h = _plan((8, 8, 8), 4)
+    try:
+        with pytest.raises(md.MdfftError):
+            md.mdfft_plan_tuning(h, 3)
+    finally:
+        md.mdfft_destroy(h)
