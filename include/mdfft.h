@@ -431,6 +431,12 @@ mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas);
  * only while fewer are outstanding, so requests arriving meanwhile share the
  * next step instead of each adding nearly empty ones. */
 mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth);
+/* At most this many consecutive tiles (1..64, default 4) are dealt to a CTA
+ * of the persistent kernel at a time; each step deals chunks of its tile
+ * count / grid, between 1 and this maximum, so that small steps still use
+ * every CTA.  Larger chunks mean fewer item lookups, smaller ones evener
+ * load.  Results do not depend on it. */
+mdfft_status mdfft_server_set_chunk(mdfft_server_t s, int chunk);
 mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out);
 mdfft_status mdfft_server_destroy(mdfft_server_t s);
 

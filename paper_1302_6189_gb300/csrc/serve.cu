@@ -53,7 +53,7 @@ struct Item {
 
 struct Table {
     int n;
-    int pad;
+    int chunk;      // consecutive tiles dealt to a CTA at a time
     int64_t total;  // tiles in the step
     Item items[kMaxItems];
 };
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, 4) serve_kernel(const Table *tab) {
     // different line lengths even out across CTAs, and consecutive tiles of
     // a chunk mostly belong to one item, so item lookups and argument copies
     // are rare (items are in increasing tile order, so lookups only advance)
-    constexpr int kChunk = 4;
+    const int kChunk = tab->chunk;
     int cur = 0;
     int64_t cur_start = 0, cur_end = n > 1 ? tab->items[1].start : total;  // item 0 starts at tile 0
     int kind = -1;
@@ -238,6 +238,7 @@ struct mdfft_server_s {
     std::unordered_map<int64_t, Request *> requests;
     int64_t next_id = 1;
     int depth = 2;  // steps in flight on the GPU at most; arrivals in between join the next step
+    int chunk = 4;  // at most this many consecutive tiles dealt to a CTA at a time
     Slot slots[kSlots];
     int next_slot = 0;
     cudaEvent_t t0 = nullptr;
@@ -483,6 +484,8 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         }
     }
     tab->n = n;
+    // the step's tiles spread over every CTA first: chunks of total / grid tiles, at most s->chunk
+    tab->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(s->chunk, total / std::max(1, s->grid)));
     tab->total = total;
     cudaError_t e = cudaSuccess;
     if (n > 0) {
@@ -621,6 +624,12 @@ mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas) {
     s->grid = ctas;
     s->stats.grid_ctas = ctas;
     return capture_graphs(s);
+}
+
+mdfft_status mdfft_server_set_chunk(mdfft_server_t s, int chunk) {
+    if (!s || chunk < 1 || chunk > 64) return fail(MDFFT_E_ARG, "chunk must be in [1, 64]");
+    s->chunk = chunk;
+    return MDFFT_OK;
 }
 
 mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth) {

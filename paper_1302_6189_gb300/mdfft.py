@@ -97,6 +97,7 @@ SIGNATURES = {
     "mdfft_server_reset_clock": (c_int, [c_void_p]),
     "mdfft_server_set_grid": (c_int, [c_void_p, c_int]),
     "mdfft_server_set_depth": (c_int, [c_void_p, c_int]),
+    "mdfft_server_set_chunk": (c_int, [c_void_p, c_int]),
     "mdfft_server_get_stats": (c_int, [c_void_p, P_(MdfftServerStats)]),
     "mdfft_server_destroy": (c_int, [c_void_p]),
 }
@@ -390,6 +391,10 @@ def mdfft_server_set_grid(server, ctas):
     _check(_lib.mdfft_server_set_grid(server, int(ctas)), "mdfft_server_set_grid")
 
 
+def mdfft_server_set_chunk(server, chunk):
+    _check(_lib.mdfft_server_set_chunk(server, int(chunk)), "mdfft_server_set_chunk")
+
+
 def mdfft_server_set_depth(server, depth):
     _check(_lib.mdfft_server_set_depth(server, int(depth)), "mdfft_server_set_depth")
 
@@ -597,6 +602,9 @@ class Server:
 
     def set_grid(self, ctas):
         mdfft_server_set_grid(self.handle, ctas)
+
+    def set_chunk(self, chunk):
+        mdfft_server_set_chunk(self.handle, chunk)
 
     def set_depth(self, depth):
         mdfft_server_set_depth(self.handle, depth)

@@ -149,3 +149,19 @@ def test_cancel_queued_and_in_flight_requests():
                 srv.cancel(ids[i])  # finished
     for i in (1, 3):
         assert torch.equal(outs[i], alone(shape, xs[i], -1, False))
+
+
+@pytest.mark.parametrize("chunk", [1, 16, 64])
+def test_tile_dealing_does_not_change_results(chunk):
+    shapes = mixed_shapes(12, 640 + chunk)
+    xs = [torch.from_numpy(si.uniform_complex(sh, 660 + i, np.complex64)).to(DEV) for i, sh in enumerate(shapes)]
+    outs = [torch.empty_like(x) for x in xs]
+    with md.Server(budget_bytes=1 << 30, max_inflight=16) as srv:
+        srv.set_chunk(chunk)
+        for x, y in zip(xs, outs):
+            srv.submit(x, y)
+        srv.drain()
+        with pytest.raises(md.MdfftError):
+            srv.set_chunk(0)
+    for sh, x, y in zip(shapes, xs, outs):
+        assert torch.equal(y, alone(sh, x, -1, False))
