@@ -5,8 +5,9 @@ For every complex64 line length N (up to 256) and CTA variant (default, 256 or
 512 threads) this replays the kernel's shared-memory accesses -- staged tile
 loads, every Stockham stage's reads and writes, the transposed-tile writes of
 the last stage and the store role's reads -- warp instruction by warp
-instruction, counts the wavefronts each needs (per bank, the distinct 4-byte
-words it touches), and keeps the layout with the fewest:
+instruction, counts the wavefronts each needs (8-byte accesses are served
+half a warp at a time: per half, the most distinct 4-byte words one bank
+holds), and keeps the layout with the fewest:
     pad(i) = i + i / g           (g in {8, 16, 32})
     line stride  = N + N / g + pe
     tile row     = LINES + te
@@ -63,11 +64,18 @@ def launch(n, thr, elem=8):
 
 
 def wavefronts(addrs):
-    banks = {}
-    for a in addrs:
-        for w in (2 * a, 2 * a + 1):
-            banks.setdefault(w % 32, set()).add(w)
-    return max((len(v) for v in banks.values()), default=0)
+    # 8-byte accesses are served half a warp at a time: per half, the most
+    # distinct 4-byte words any bank holds
+    total = 0
+    for half in (addrs[:16], addrs[16:]):
+        banks = {}
+        for a in half:
+            if a is None:
+                continue
+            for w in (2 * a, 2 * a + 1):
+                banks.setdefault(w % 32, set()).add(w)
+        total += max((len(v) for v in banks.values()), default=0)
+    return total
 
 
 def cost(n, thr, g, pe, te):
@@ -82,8 +90,8 @@ def cost(n, thr, g, pe, te):
     def warp_access(fn):
         nonlocal total
         for w0 in range(0, threads, 32):
-            a = [x for x in (fn(tid) for tid in range(w0, w0 + 32)) if x is not None]
-            if a:
+            a = [fn(tid) for tid in range(w0, w0 + 32)]  # lane order kept: halves are lanes 0-15, 16-31
+            if any(x is not None for x in a):
                 total += wavefronts(a)
 
     direct = tl * 8 >= 32
