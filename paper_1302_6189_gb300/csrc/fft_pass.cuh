@@ -133,6 +133,9 @@ template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };
 
 __host__ __device__ constexpr RadixPlan radix_plan_tc(int n);
+// shared state of the tensor-core stages (the DFT-16 operand, an mbarrier,
+// the TMEM base, a flag), TcShared in tc_stage.cuh
+constexpr int kTcSharedBytes = 4112;
 
 // Launch configuration of the pass kernel for line length N.  TC != 0 selects
 // the tensor-core variant (complex64 only): radix-16 stages run as GEMMs.
@@ -175,6 +178,9 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int kGrowThreads = (sizeof(Real) == 4 && TC == 0) ? 256 : kMaxThreads;
     static constexpr int lines_for() {
         if (THR) return THR / TL;
+        // tensor-core CTAs for 512-point lines: 8 lines (256 threads), so that
+        // two CTAs share an SM (16 lines take 512 threads at 128 registers)
+        if (TC && TL == 32) return 8;
         int l = kMinLines;
         while (l > 1 && TL * l > kMaxThreads) l /= 2;
         while (l < 256 && 2 * l * N <= kTileElems && 2 * TL * l <= kGrowThreads) l *= 2;
@@ -190,13 +196,19 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int PADG = LAY.g;                // pad(i) = i + i / PADG
     static constexpr int PADN = N + N / PADG + LAY.pe;  // line stride of the stage buffer
     static constexpr int TROW = LINES + LAY.te;         // row of the transposed tile
-    static constexpr int DATA = LINES * PADN > N * TROW ? LINES * PADN : N * TROW;
-    static constexpr int TWN = tw_entries(plan) > 0 ? tw_entries(plan) : 1;  // twiddle entries
-    static constexpr int BFRAG = TC ? 1024 * 4 / (int)sizeof(C) : 0;  // tensor-core B fragments (in C units)
+    static constexpr int DATA0 = LINES * PADN > N * TROW ? LINES * PADN : N * TROW;
+    // tensor-core stages write their operand rows (hi and lo, 128 B per row,
+    // whole 128-row groups) over the stage buffer; offsets stay 16-byte aligned
+    static constexpr int TC_ROWS = TC ? (TL * LINES + 127) / 128 * 128 : 0;
+    static constexpr int DATA = TC ? ((DATA0 > TC_ROWS * 16 ? DATA0 : TC_ROWS * 16) + 1) / 2 * 2 : DATA0;
+    static constexpr int TWN0 = tw_entries(plan) > 0 ? tw_entries(plan) : 1;  // twiddle entries
+    static constexpr int TWN = TC ? (TWN0 + 1) / 2 * 2 : TWN0;
+    static constexpr int BFRAG = TC ? kTcSharedBytes / (int)sizeof(C) : 0;  // tensor-core shared state (C units)
     // + the input offset of every tile line and the tile's coordinates (4 int64)
     static constexpr size_t SMEM = (size_t)(DATA + TWN + BFRAG) * sizeof(C) + (size_t)(LINES + 4) * sizeof(int64_t);
-    // first stage loads from HBM directly (tensor-core stages read shared memory)
-    static constexpr bool DIRECT = TC == 0 && TL * (int)sizeof(C) >= 32;
+    // first stage loads from HBM directly (always for tensor-core plans, whose
+    // first stage is a radix-16 GEMM with one butterfly per thread)
+    static constexpr bool DIRECT = TC != 0 || TL * (int)sizeof(C) >= 32;
 };
 
 // ------------------------------------------------------------------ complex helpers
@@ -355,19 +367,23 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
 
     // gsrc: this thread's line in HBM (first stage, direct loads) or null.
     // after_first() runs once the first stage is done with its source (all
-    // threads, after the stage's closing barrier).
+    // threads, after the stage's closing barrier).  tc_par: parity of the
+    // tensor-core mbarrier phase at the tile's first radix-16 stage.
     template <class Hook = NoHook>
     __device__ __forceinline__ static void run(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
-                                               bool ok, bool conj, bool active, const Hook &after_first = Hook()) {
+                                               bool ok, bool conj, bool active, const Hook &after_first = Hook(),
+                                               uint32_t tc_par = 0) {
         if constexpr (TC != 0 && R == 16) {
             tc_radix16_stage<TC, N, Cfg::LINES, Cfg::THREADS, Cfg::PADN, Cfg::TROW, NS, LAST>(
-                buf, tile, tw + TWOFF, reinterpret_cast<const uint32_t *>(tw + Cfg::TWN), active);
+                buf, tile, tw + TWOFF, reinterpret_cast<TcShared *>(const_cast<C *>(tw) + Cfg::TWN), active, gsrc, ok,
+                conj, tc_par ^ (uint32_t)(SI & 1));
         } else {
             simt(buf, tile, tw, gsrc, line, t, ok, conj);
         }
         if constexpr (FIRST) after_first();
         if constexpr (!LAST)
-            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active);
+            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active, NoHook(),
+                                                               tc_par);
     }
 
     __device__ __forceinline__ static void simt(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
@@ -555,7 +571,8 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
 
 // The whole pass for one tile of lines.  Threads tid >= THREADS (a CTA shared
 // by several line lengths, see the grouped serving kernel) take part in the
-// barriers only.
+// barriers only.  (Tensor-core plans use the persistent kernel of
+// tc_pass.cuh instead.)
 template <typename Real, int N, int TC, int THR = 0>
 __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned char *smem_raw, const int tid) {
     using Cfg = PassCfg<Real, N, TC, THR>;
@@ -579,10 +596,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
             lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
         }
     }
-    if (active) {
+    if (active)
         for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
-        if constexpr (TC != 0) tc_build_bfrag<TC, Cfg::THREADS>(reinterpret_cast<uint32_t *>(tw + Cfg::TWN), tid);
-    }
     __syncthreads();
     const TileCoord c = *shc;
 

@@ -19,67 +19,9 @@
 #pragma once
 
 #include "fft_pass.cuh"
+#include "ptx_sync.cuh"
 
 namespace mdfft {
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-        "r"(bytes)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbarrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ uint64_t global_timer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// true if the phase of the given parity completed within limit_ns
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_timer_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_timer_ns() - t0 > limit_ns) return false;
-    return true;
-}
 
 template <int N, int NBUF> struct PipeCfg {
     using Cfg = PassCfg<float, N, 0, 0>;
@@ -91,10 +33,10 @@ template <int N, int NBUF> struct PipeCfg {
     static constexpr uint64_t kWaitLimitNs = 2000000000ull;
 };
 
-// Warp 0: arm barrier b with the byte count of tile t and copy its valid lines.
-template <int N>
+// Warp 0: arm barrier b with the byte count of tile t and copy its valid
+// lines (a tile of LINES lines of N complex64).
+template <int N, int LINES = PassCfg<float, N, 0, 0>::LINES>
 __device__ __forceinline__ void pipe_issue(const PassArgs &a, int64_t t, float2 *land, uint64_t *bar, int lane) {
-    using Cfg = PassCfg<float, N, 0, 0>;
     const TileCoord c = tile_coords(a, t);
     const int64_t vg = a.Ng - c.g0 < a.Bg ? a.Ng - c.g0 : a.Bg;
     const int64_t vh = a.Nh - c.h0 < a.Bh ? a.Nh - c.h0 : a.Bh;
@@ -104,7 +46,7 @@ __device__ __forceinline__ void pipe_issue(const PassArgs &a, int64_t t, float2 
     }
     __syncwarp();
     const float2 *in = reinterpret_cast<const float2 *>(a.in);
-    for (int l = lane; l < Cfg::LINES; l += 32) {
+    for (int l = lane; l < LINES; l += 32) {
         const int bg = l % a.Bg, bh = l / a.Bg;
         if (l < a.Bg * a.Bh && bg < vg && bh < vh)
             bulk_copy_g2s(land + (size_t)l * N, in + c.in_base + bg * a.in_sg + bh * a.in_sh,

@@ -222,7 +222,7 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     a.own_out = owner_map(M, p->N, p->P, Lo);
     a.scale = 1.0;
     a.scaled = 0;
-    ps.grid = ps.ctas;
+    ps.grid = ps.k.persistent ? std::min<int64_t>(ps.ctas, wave) : ps.ctas;
     return MDFFT_OK;
 }
 
@@ -231,13 +231,36 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
 // computed in FP64 with sincospi and rounded to the pass precision.
 }  // namespace
 
+// Resident CTAs of kernel k on the whole GPU (the runtime's occupancy
+// figure).  A persistent kernel launches exactly this many CTAs, so it asks
+// for the largest shared-memory carveout (a property of the function) and the
+// count is also worked out from its registers and shared memory against the
+// SM's limits; the larger figure is used.  (The runtime reported one CTA per
+// SM for the tensor-core kernels, whose limits allow three.)
 int64_t mdfft::detail::wave_ctas(const PassKernel &k) {
-    int dev = 0, sms = 1, per = 1;
+    int dev = 0, sms = 1, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (k.smem > 48 * 1024) cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.fn, k.threads, k.smem) != cudaSuccess || per < 1) per = 1;
-    return (int64_t)sms * per;
+    if (k.persistent && k.smem > 48 * 1024)
+        cudaFuncSetAttribute(k.fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.fn, k.threads, k.smem) != cudaSuccess) per = 0;
+    if (!k.persistent) return (int64_t)sms * std::max(per, 1);
+    cudaFuncAttributes fa;
+    int smem_sm = 0, regs_sm = 0, thr_sm = 0, reserved = 0;
+    if (cudaFuncGetAttributes(&fa, k.fn) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+        const int warps = (k.threads + 31) / 32;
+        const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+        const int by_smem = smem_sm / (int)(k.smem + fa.sharedSizeBytes + reserved);
+        const int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : 32;
+        const int by_thr = thr_sm / k.threads;
+        per = std::max(per, std::min(by_smem, std::min(by_regs, by_thr)));
+    }
+    return (int64_t)sms * std::max(per, 1);
 }
 
 void mdfft::detail::retile_pass(const mdfft_plan_s *p, int s, int lines, PassArgs *out, int64_t *ctas) {
@@ -332,8 +355,8 @@ mdfft_status check_exec(mdfft_plan_t p, const void *in, const void *out, int dir
         return fail(MDFFT_E_ARG, "in == out needs a plan made with MDFFT_PLAN_INPLACE");
     if (!inplace && overlaps(in, out, bytes)) return fail(MDFFT_E_ARG, "in and out overlap partially");
     if (counts && ((uintptr_t)counts % 8)) return fail(MDFFT_E_ARG, "misaligned counts pointer");
-    for (int s = 0; s < p->M; ++s)  // persistent pipelined passes copy whole 16-byte units
-        if (p->pass[s].k.persistent && (((uintptr_t)in % 16) || ((uintptr_t)out % 16)))
+    for (int s = 0; s < p->M; ++s)  // pipelined passes copy whole 16-byte units
+        if (p->pass[s].k.bulk && (((uintptr_t)in % 16) || ((uintptr_t)out % 16)))
             return fail(MDFFT_E_ARG, "tuned pass kernels read whole 16-byte units: align in and out to 16 bytes");
     return MDFFT_OK;
 }

@@ -12,6 +12,7 @@ template <int N, int NBUF> static PassKernel make_pipe() {
     PassKernel k{(const void *)&fft_pass_pipe_kernel<N, NBUF>, Cfg::THREADS, Cfg::LINES, Cfg::TL,
                  PipeCfg<N, NBUF>::SMEM, Cfg::plan};
     k.persistent = NBUF;
+    k.bulk = 1;
     return k;
 }
 

@@ -1,13 +1,17 @@
-// pass_tc.cu -- instantiations of the fused pass kernel with tensor-core radix-16 stages
-// (complex64 data; split hi/lo FP16 or BF16 operands, FP32 accumulation).
+// pass_tc.cu -- instantiations of the persistent pass kernel with tensor-core radix-16
+// stages (complex64 data; split hi/lo FP16 or BF16 operands, FP32 accumulation).
 #include "passes.h"
+#include "tc_pass.cuh"
 
 namespace mdfft {
 
 template <int N, int TC> static PassKernel make_tc() {
     using Cfg = PassCfg<float, N, TC>;
-    return PassKernel{(const void *)&fft_pass_kernel<float, N, TC>, Cfg::THREADS, Cfg::LINES, Cfg::TL, Cfg::SMEM,
-                      Cfg::plan};
+    PassKernel k{(const void *)&fft_pass_tc_kernel<N, TC>, Cfg::THREADS, Cfg::LINES, Cfg::TL, TcPassCfg<N, TC>::SMEM,
+                 Cfg::plan};
+    k.persistent = 1;
+    k.bulk = 1;
+    return k;
 }
 
 bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k) {

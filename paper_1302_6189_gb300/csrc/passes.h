@@ -32,7 +32,8 @@ struct PassKernel {
     int threads, lines, tl;
     size_t smem;
     RadixPlan plan;      // radix plan of the kernel; its twiddle table follows tw_offset()
-    int persistent = 0;  // > 0: walks tiles with a grid stride (launch at most one wave); landing buffers
+    int persistent = 0;  // > 0: walks tiles with a grid stride (launch at most one wave)
+    int bulk = 0;        // 1: loads lines with bulk copies (input and output 16-byte aligned)
 };
 
 bool find_pass_kernel_c64(int64_t n, PassKernel *k);
