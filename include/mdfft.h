@@ -62,7 +62,8 @@ typedef enum {
 typedef enum {
     MDFFT_C64 = 0,         /* complex64, FP32 arithmetic */
     MDFFT_C128 = 1,        /* complex128, FP64 arithmetic */
-    MDFFT_C64_TC_FP16 = 2, /* complex64 in/out; radix-16 stages on tensor cores, split hi/lo FP16, FP32 accumulate */
+    MDFFT_C64_TC_FP16 = 2, /* complex64 in/out; radix-16 stages as tcgen05 GEMMs, split hi/lo FP16, FP32
+                              accumulators in TMEM (persistent kernel: arrays 16-byte aligned) */
     MDFFT_C64_TC_BF16 = 3  /* as above with BF16 hi/lo operands */
 } mdfft_dtype;
 
@@ -347,8 +348,9 @@ mdfft_status mdfft_pattern_probe(mdfft_plan_t plan, int s, const void *in_dev, v
 
 /* Waits for the device and reports whether a pass kernel of this plan gave up
  * a bounded wait since the last check (MDFFT_E_TIMEOUT; the affected output
- * is incomplete).  Only the persistent pipelined kernels that
- * mdfft_plan_autotune may select wait on the device. */
+ * is incomplete).  The kernels that wait on the device are the persistent
+ * pipelined kernels that mdfft_plan_autotune may select and the tensor-core
+ * kernels of MDFFT_C64_TC_FP16 / _BF16 plans (bulk copies, MMA completion). */
 mdfft_status mdfft_plan_check(mdfft_plan_t plan);
 
 /* Device workspace the plan owns, in bytes (0 for host-only plans). */

@@ -360,6 +360,21 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
     // stage writes the transposed tile across lines and needs the CTA barrier;
     // so does a landing buffer, refilled for every warp after the first stage)
     static constexpr bool WARP_LOCAL = TC == 0 && 32 % Cfg::TL == 0 && SRC != 2;
+    // tensor-core plans (radix-16 stages first; see tc_radix16_stage): later
+    // radix-16 stages write their operand rows into the landing buffer; a
+    // stage that is not the last closes with a warp barrier when every line
+    // lies in one warp; the landing buffer is refilled once its last reader
+    // is done (after the first stage's operand rows are written when only
+    // the first stage is radix 16, else after the last radix-16 stage's MMAs)
+    static constexpr int TC_LAST = [] {
+        int l = -1;
+        for (int i = 0; i < Cfg::plan.S; ++i)
+            if (Cfg::plan.R[i] == 16) l = i;
+        return l;
+    }();
+    static constexpr bool TC_A_LAND = TC != 0 && !FIRST;
+    static constexpr bool TC_END_CTA = LAST || !(Cfg::TL <= 32 && 32 % Cfg::TL == 0);
+    static constexpr int TC_HOOK = TC_LAST == 0 ? (SI == 0 ? 1 : 0) : (SI == TC_LAST ? 2 : 0);
 
     struct NoHook {
         __device__ __forceinline__ void operator()() const {}
@@ -367,23 +382,25 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
 
     // gsrc: this thread's line in HBM (first stage, direct loads) or null.
     // after_first() runs once the first stage is done with its source (all
-    // threads, after the stage's closing barrier).  tc_par: parity of the
+    // threads, after the stage's closing barrier; in tensor-core plans, once
+    // the landing buffer's last reader is done, see TC_HOOK).  tc_par: parity of the
     // tensor-core mbarrier phase at the tile's first radix-16 stage.
     template <class Hook = NoHook>
     __device__ __forceinline__ static void run(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,
                                                bool ok, bool conj, bool active, const Hook &after_first = Hook(),
                                                uint32_t tc_par = 0) {
         if constexpr (TC != 0 && R == 16) {
-            tc_radix16_stage<TC, N, Cfg::LINES, Cfg::THREADS, Cfg::PADN, Cfg::TROW, NS, LAST>(
-                buf, tile, tw + TWOFF, reinterpret_cast<TcShared *>(const_cast<C *>(tw) + Cfg::TWN), active, gsrc, ok,
-                conj, tc_par ^ (uint32_t)(SI & 1));
+            tc_radix16_stage<TC, N, Cfg::LINES, Cfg::THREADS, Cfg::PADN, Cfg::TROW, NS, LAST, TC_A_LAND,
+                             TC_END_CTA, TC_HOOK>(buf, tile, tw + TWOFF,
+                                                  reinterpret_cast<TcShared *>(const_cast<C *>(tw) + Cfg::TWN), active,
+                                                  gsrc, ok, conj, tc_par ^ (uint32_t)(SI & 1), after_first);
         } else {
             simt(buf, tile, tw, gsrc, line, t, ok, conj);
+            if constexpr (FIRST) after_first();
         }
-        if constexpr (FIRST) after_first();
         if constexpr (!LAST)
-            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active, NoHook(),
-                                                               tc_par);
+            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active,
+                                                               after_first, tc_par);
     }
 
     __device__ __forceinline__ static void simt(C *buf, C *tile, const C *tw, const C *gsrc, int line, int t,

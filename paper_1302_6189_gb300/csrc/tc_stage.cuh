@@ -244,11 +244,25 @@ template <int THREADS> __device__ __forceinline__ void tc_end(TcShared *ts, int 
 // (in the landing buffer of the persistent kernel, or in HBM), ok false for
 // lines outside the array (zeros), conj conjugates the loaded values; later
 // stages read the stage buffer.
-template <int TC, int N, int LINES, int THREADS, int PADN, int TROW, int NS, bool LAST>
+//
+// A_LAND: the operand rows go to the landing buffer (LINES x N complex64 right
+// before the stage buffer in fft_pass_tc_kernel; free once the first stage
+// has read it) instead of over the stage buffer, so no barrier is needed
+// between reading the stage buffer and writing them.  END_CTA: close with a
+// CTA barrier (else a warp barrier: the next stage reads only lines that this
+// warp wrote).  HOOK: when to call hook() (warp 0 refills the landing buffer):
+// 1 right after the operand rows are written (the first stage's source is
+// consumed), 2 right after the MMAs completed (operand rows in the landing
+// buffer consumed), 0 never.
+template <int TC, int N, int LINES, int THREADS, int PADN, int TROW, int NS, bool LAST, bool A_LAND, bool END_CTA,
+          int HOOK, class Hook>
 __device__ __forceinline__ void tc_radix16_stage(float2 *buf, float2 *tile, const float2 *tw, TcShared *ts,
-                                                 bool active, const float2 *gsrc, bool ok, bool conj,
-                                                 uint32_t parity) {
+                                                 bool active, const float2 *gsrc, bool ok, bool conj, uint32_t parity,
+                                                 const Hook &hook) {
     constexpr bool FIRST = NS == 1;
+    static_assert(!(FIRST && A_LAND), "the first stage reads the landing buffer");
+    static_assert(!A_LAND || (size_t)LINES * N * sizeof(float2) >= (size_t)(THREADS + 127) / 128 * 2 * kTcGroupBytes,
+                  "operand rows must fit the landing buffer");
     using T = TcTypes<TC>;
     using Geom = TcGeom<THREADS>;
     constexpr int NB = N / 16;
@@ -287,9 +301,10 @@ __device__ __forceinline__ void tc_radix16_stage(float2 *buf, float2 *tile, cons
             for (int r = 0; r < 16; ++r) v[r].x *= sc, v[r].y *= sc;
         }
     }
-    if constexpr (!FIRST) __syncthreads();  // every read of the stage buffer before the operand rows overwrite it
+    // every read of the stage buffer before the operand rows overwrite it
+    if constexpr (!FIRST && !A_LAND) __syncthreads();
 
-    unsigned char *A = reinterpret_cast<unsigned char *>(buf);
+    unsigned char *A = reinterpret_cast<unsigned char *>(buf) - (A_LAND ? (size_t)LINES * N * sizeof(float2) : 0);
     if (active) {
         unsigned char *row = A + (tid >> 3) * kTcSbo + (tid & 7) * 16;
 #pragma unroll
@@ -305,7 +320,9 @@ __device__ __forceinline__ void tc_radix16_stage(float2 *buf, float2 *tile, cons
         }
     }
     fence_proxy_async_shared();  // the operand rows (and B) visible to the tensor cores
+    tc_fence_before();           // earlier TMEM reads of this thread before the MMAs below
     __syncthreads();
+    if constexpr (HOOK == 1) hook();
 
     if (tid == 0) {
         tc_fence_after();
@@ -337,6 +354,7 @@ __device__ __forceinline__ void tc_radix16_stage(float2 *buf, float2 *tile, cons
         tc_fence_before();
     }
     __syncthreads();
+    if constexpr (HOOK == 2) hook();
     if (ts->failed) return;  // uniform: written before the barrier
     if (active) {  // warp-uniform
         uint32_t d[32];
@@ -354,7 +372,8 @@ __device__ __forceinline__ void tc_radix16_stage(float2 *buf, float2 *tile, cons
         }
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (END_CTA) __syncthreads();
+    else __syncwarp();
 }
 
 }  // namespace mdfft
