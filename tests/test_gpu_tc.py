@@ -105,3 +105,46 @@ def test_tc_batched_and_last_layout(dt):
     for b in range(B):
         ref = oracle.fftn(vols[b])
         assert rel_l2(y[b].cpu().numpy().astype(np.complex128), ref) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c64_tc_fp16", "c64_tc_bf16"])
+def test_tc_persistent_passes_counts_and_status(dt):
+    # every pass of this shape is a tensor-core pass: persistent (at most one
+    # resident wave, several tiles per CTA); count mode adds the oracle's
+    # amounts per volume, no bounded wait gives up, and the spectra hold
+    shape, P, B = (64, 48, 32), 24, 2
+    vols = [si.gaussian_complex(shape, 950 + b) for b in range(B)]
+    x = torch.from_numpy(np.stack([v.astype(np.complex64) for v in vols])).to(DEV)
+    with md.Plan(shape, P, None, dt, batch=B) as pl:
+        passes = pl.describe()
+        assert all(p["persistent"] == 1 and 1 <= p["grid"] <= p["ctas"] for p in passes), passes
+        _, counts = pl.exec_counted(x)
+        y = pl.exec(x)
+        back = pl.exec(y, dir=+1, normalize=True)
+        torch.cuda.synchronize()
+        pl.check()
+        c = counts.cpu().tolist()
+        order = pl.order()
+    ref = oracle.comm_volume(shape, P, order)
+    assert c[:2] == [B * v for v in ref["per_transition"]]
+    assert c[2] == B * ref["final_to_natural"]
+    assert c[3:] == [B * v for v in ref["split_line"]]
+    for b in range(B):
+        assert rel_l2(y[b].cpu().numpy().astype(np.complex128), oracle.fftn(vols[b])) < TOL[dt]
+        assert rel_l2(back[b].cpu().numpy().astype(np.complex128), vols[b]) < 2 * TOL[dt]
+
+
+def test_tc_plans_need_16_byte_alignment():
+    # the tensor-core kernel copies whole lines with bulk copies: refused on
+    # the host before any launch
+    shape = (32, 48, 16)
+    T = 32 * 48 * 16
+    with md.Plan(shape, 4, None, "c64_tc_fp16") as plan:
+        buf = torch.zeros(T + 2, dtype=torch.complex64, device=DEV)
+        out = torch.zeros(T + 2, dtype=torch.complex64, device=DEV)
+        with pytest.raises(md.MdfftError) as e:
+            md.mdfft_exec(plan.handle, buf.data_ptr() + 8, out.data_ptr(), -1, 0, 0)
+        assert e.value.status == -1
+        with pytest.raises(md.MdfftError) as e:
+            md.mdfft_exec(plan.handle, buf.data_ptr(), out.data_ptr() + 8, -1, 0, 0)
+        assert e.value.status == -1
