@@ -17,11 +17,12 @@
 // Every thread of the CTA owns one butterfly row (the tile has exactly as many
 // radix-16 butterflies as the CTA has threads).  Per stage:
 //  1. each thread reads its 16 inputs (from the tile's landing buffer in the
-//     first stage, else from the stage buffer), twiddles, scales
-//     and splits them, and writes its A row (hi and lo) into shared memory in
-//     the no-swizzle K-major layout of the tensor cores (8-row x 16-byte core
-//     matrices); the operand rows alias the stage buffer, whose inputs are
-//     all in registers by then;
+//     first stage, else from the stage buffer), twiddles, scales and splits
+//     them, and writes its A row (hi and lo) into shared memory in the
+//     no-swizzle K-major layout of the tensor cores (8-row x 16-byte core
+//     matrices): over the stage buffer in the first stage (its old contents
+//     are no longer needed), into the landing buffer (consumed by then) in
+//     the later ones;
 //  2. one thread issues, per 128-row group, 2 k-steps x 3 products of
 //     tcgen05.mma (M = 128, N = 32, K = 16) into a 32-column TMEM
 //     accumulator and commits them to an mbarrier;
@@ -241,9 +242,8 @@ template <int THREADS> __device__ __forceinline__ void tc_end(TcShared *ts, int 
 //   and writes y[(j / NS) 16 NS + j mod NS + q NS].
 // parity: which phase of the mbarrier this stage's commit completes.
 // The first stage (NS = 1) reads its butterfly from gsrc, the thread's line
-// (in the landing buffer of the persistent kernel, or in HBM), ok false for
-// lines outside the array (zeros), conj conjugates the loaded values; later
-// stages read the stage buffer.
+// in the tile's landing buffer, ok false for lines outside the array (zeros),
+// conj conjugates the loaded values; later stages read the stage buffer.
 //
 // A_LAND: the operand rows go to the landing buffer (LINES x N complex64 right
 // before the stage buffer in fft_pass_tc_kernel; free once the first stage
