@@ -42,6 +42,12 @@ template <int N, int TC> struct TcPassCfg {
     // warps); without a bound the compiler picked a register cap that spilled
     // hundreds of bytes per thread for some lengths
     static constexpr int MIN_BLOCKS = 768 / Cfg::THREADS > 1 ? 768 / Cfg::THREADS : 1;
+    // shared memory per SM (228 KiB, 1 KiB of it reserved per CTA) and per CTA (227 KiB)
+    static constexpr int MAX_RESIDENT = (int)(233472 / (SMEM + 1024));
+    static_assert(SMEM <= 232448, "tile does not fit one CTA's shared memory");
+    // the TMEM columns of all CTAs that can share an SM fit its 512 columns, so
+    // tcgen05.alloc never waits on another CTA
+    static_assert(TcGeom<Cfg::THREADS>::COLS * MAX_RESIDENT <= 512, "TMEM columns of the resident CTAs");
 };
 
 template <int N, int TC>
