@@ -40,8 +40,11 @@ METRIC = "M-D FFT GB/s & % HBM peak vs plain; served FFT/s, p50/p99 at stated er
 SHAPE = (256, 256, 256)
 P_DEFAULT = 4096
 PROFILE = os.path.join(ROOT, "profiles", "fft_pass_256cubed_c64.md")
+# everything the complex64 pass kernel is compiled from: its source, every
+# header it includes, and the build script that holds the nvcc flags
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1302_6189_gb300", "csrc", f) for f in
-                  ("fft_pass.cuh", "pass_c64.cu")]
+                  ("fft_pass.cuh", "pass_c64.cu", "smem_layout.h", "tc_stage.cuh", "ptx_sync.cuh", "passes.h")] + \
+                 [os.path.join(ROOT, "paper_1302_6189_gb300", "build.py")]
 
 
 def parse_args():
@@ -59,13 +62,27 @@ def parse_args():
                          "(3 + 3 pass launches), for ncu captures")
     ap.add_argument("--profile-batch", type=int, default=8, help="volumes per launch in --profile-case")
     ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
+    ap.add_argument("--profile-shape", default="256,256,256", help="grid of --profile-case, e.g. 64,64,64,64")
     ap.add_argument("--serving-only", type=int, default=0, metavar="REQUESTS",
                     help="run only the serving study with this many requests and print it")
     ap.add_argument("--serving-budget-gb", type=float, default=40.0)
     return ap.parse_args()
 
 
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector) rate, nominal
+PROFILE_C128 = os.path.join(ROOT, "profiles", "fft_pass_256cubed_c128.md")
+
+
+def fp64_peak(dev):
+    """The device's FP64 multiply-add rate in TFLOP/s, measured by the
+    library's probe kernel (CUDA events; 8 waves of 256-thread CTAs)."""
+    import torch
+
+    from paper_1302_6189_gb300 import mdfft_fp64_rate_probe
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctas = sms * 8 * 8
+    out = torch.empty(ctas * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    return max(mdfft_fp64_rate_probe(out.data_ptr(), ctas, 4096, stream) for _ in range(3))
 
 
 def kernel_hash():
@@ -76,25 +93,35 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def profile_values(path=PROFILE):
+    """The `key: value` lines (traffic_bytes_*, dp_*) of a committed ncu
+    summary, if it was taken on the current kernel sources (else {})."""
     try:
-        with open(PROFILE) as f:
+        with open(path) as f:
             text = f.read()
     except OSError:
-        return None
+        return {}
     kv = {}
     for line in text.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256")):
-            k, v = line.split(":", 1)
+        t = line.strip()
+        if ":" in t and t.startswith(("traffic_bytes", "kernel_source_sha256", "dp_")):
+            k, v = t.split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if kv.get("kernel_source_sha256") != kernel_hash():
-        return None
-    try:
-        return int(float(kv["traffic_bytes_per_launch"]))
-    except (KeyError, ValueError):
-        return None
+    if kv.pop("kernel_source_sha256", None) != kernel_hash():
+        return {}
+    out = {}
+    for k, v in kv.items():
+        try:
+            out[k] = int(float(v))
+        except ValueError:
+            pass
+    return out
+
+
+def profile_traffic(path=PROFILE, key="traffic_bytes_per_launch"):
+    """DRAM bytes per launch from a committed ncu summary taken on the current
+    kernel sources (else None)."""
+    return profile_values(path).get(key)
 
 
 def peaks():
@@ -244,17 +271,56 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(shape, elem):
+def oracle_spectrum(x, nthreads):
+    """The FP64 oracle's forward transform of the host array x, and its wall
+    time: the checker the GPU results of the bench are stated against (this
+    and cpu_baseline are the only places the bench runs the oracle)."""
+    import numpy as np
+
+    import oracle
+    y = np.array(x, dtype=np.complex128, order="C")
+    t0 = time.perf_counter()
+    oracle.fftn_inplace(y, -1, nthreads)
+    return y, time.perf_counter() - t0
+
+
+def errors_vs(y, ref):
+    """rel-L2 of y against ref and the largest element error over ref's RMS
+    (accumulated slab by slab along the first axis)."""
+    import numpy as np
+    num = den = emax = 0.0
+    for i in range(0, y.shape[0], 32):
+        d = np.abs(y[i:i + 32].astype(np.complex128) - ref[i:i + 32])
+        r = np.abs(ref[i:i + 32])
+        num += float(np.sum(d * d))
+        den += float(np.sum(r * r))
+        emax = max(emax, float(d.max()))
+    rms = (den / ref.size) ** 0.5
+    return {"rel_l2": (num / den) ** 0.5, "max_err_over_rms": emax / rms}
+
+
+def cpu_baseline(shape, elem, fwd0=None):
+    """The oracle timed on the host cores (forward + inverse of one volume);
+    with fwd0 (the GPU forward spectrum of volume 0 of the bench workload) also
+    the error of that result against the oracle's."""
     nthreads = len(os.sched_getaffinity(0))
     # about 20 s of CPU work: one forward + inverse takes ~0.25 s on 16 cores
     reps = max(2, min(12, int(round(80 / max(1, nthreads)))))
     times = oracle_fwd_inv_seconds(shape, reps, nthreads)
     per_step, _ = algorithmic_bytes(shape, elem)
     gbs = 2 * per_step * reps / sum(times) / 1e9
-    return {"value": round(gbs, 3), "unit": "GB/s", "cores": nthreads, "kind": "oracle",
-            "sample": f"{reps} x (forward + inverse) of one {'x'.join(map(str, shape))} volume, FP64 oracle "
-                      f"(complex128) on {nthreads} host threads; bytes counted as for the complex64 GPU path",
-            "seconds": round(sum(times), 3), "cpu": cpu_model()}
+    out = {"value": round(gbs, 3), "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+           "sample": f"{reps} x (forward + inverse) of one {'x'.join(map(str, shape))} volume, FP64 oracle "
+                     f"(complex128) on {nthreads} host threads; bytes counted as for the complex64 GPU path",
+           "seconds": round(sum(times), 3), "cpu": cpu_model()}
+    if fwd0 is not None:
+        import numpy as np
+
+        import synth_inputs as si
+        x = si.uniform_complex(shape, si.SEEDS["cube256"]).astype(np.complex64)  # the GPU's input, widened
+        ref, _ = oracle_spectrum(x, nthreads)
+        out["forward_vs_oracle_volume0"] = errors_vs(fwd0, ref)
+    return out
 
 
 def run_reference(args):
@@ -360,6 +426,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     nvtx.range_pop()
     err = float((torch.linalg.vector_norm(zs[0] - xs[0]) / torch.linalg.vector_norm(xs[0])).item())
+    fwd0 = ys[0].cpu().numpy()  # forward spectrum of volume 0 (checked against the oracle in the CPU leg)
     # forward error of volume 0 against the complex128 GPU path of the same order
     with Plan(shape, P, order, "c128") as p128:
         ref = p128.exec(xs[0].to(torch.complex128))
@@ -429,14 +496,14 @@ def run_ours(args):
 
     extra = None
     if not args.no_extra and world == 1:  # single-GPU studies: not repeated on every rank of a replica run
-        extra = extra_table(dev, xs, P)
+        extra = extra_table(dev, xs, P, with_oracle=not args.no_cpu)
 
     if rank != 0:
         barrier(world)
         return
     cpu = None
     if world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(shape, elem)
+        cpu = cpu_baseline(shape, elem, fwd0)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
@@ -485,7 +552,7 @@ def _orders3():
     return out
 
 
-def extra_table(dev, x, P):
+def extra_table(dev, x, P, with_oracle=True):
     """GB/s of every 3-D transpose order (complex64) and of the best order in
     complex128, a batch of 256^3 volumes (x: [B, 256, 256, 256]) per launch,
     forward transforms, 10 timed reps each."""
@@ -526,15 +593,26 @@ def extra_table(dev, x, P):
         pass_ms, _ = pl.pass_times()
     flops = 5.0 * T * 24 * B  # nominal 5 T log2 T per volume
     fp64_tflops = flops / (ms * 1e-3) / 1e12
+    peak64 = fp64_peak(dev)
+    # FP64 operations the pass kernel executes, counted by ncu (multiply-adds
+    # x 2 + adds + multiplies per launch of one volume), if that count was
+    # taken on the current kernel sources
+    counted = profile_values(PROFILE_C128).get("dp_flops_per_launch")
+    avg_pass_ms = sum(pass_ms) / len(pass_ms)
+    counted_tflops = None if counted is None else B * counted / (avg_pass_ms * 1e-3) / 1e12
     res["c128"] = {"gbs": round(2 * per_transform / (ms * 1e-3) / 1e9, 1), "ms_per_transform": round(ms / B, 4),
                    "nominal_tflops_fp64": round(fp64_tflops, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms],
-                   # FP64-bound: nominal 5 T log2 T work against GB300's nominal FP64 rate (no measured FP64 peak)
-                   "roofline": {"bound": "alu", "achieved": round(fp64_tflops, 3), "peak": FP64_NOMINAL_TFLOPS,
-                                "peak_kind": "nominal", "unit": "TFLOP/s",
-                                "frac": round(fp64_tflops / FP64_NOMINAL_TFLOPS, 3)}}
+                   # FP64-bound: the executed FP64 operations per second against the measured FP64 rate
+                   "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": round(peak64, 3),
+                                "peak_kind": "measured (mdfft_fp64_rate_probe: independent multiply-add chains)",
+                                "achieved": None if counted_tflops is None else round(counted_tflops, 3),
+                                "frac": None if counted_tflops is None else round(counted_tflops / peak64, 3),
+                                "dp_flops_per_launch_per_volume": counted,
+                                "achieved_nominal_5TlogT": round(fp64_tflops, 3),
+                                "frac_nominal_work": round(fp64_tflops / peak64, 3)}}
     res["small_32cubed_c128"] = small_study(dev)
-    res["precision_512cubed"] = precision_study(dev)
+    res["precision_512cubed"] = precision_study(dev, with_oracle)
     res["md_4d_5d"] = md_study(dev)
     res["decompositions"] = decomposition_study(dev)
     res["serving"] = serving_study(dev)
@@ -610,11 +688,38 @@ def md_study(dev, reps=10):
                     torch.cuda.synchronize(dev)
                     ms = a.elapsed_time(b) / reps
                     pass_ms, _ = pl.pass_times()
-                out[f"{'x'.join(map(str, shape))} P={P} {'worst' if want else 'best'}"] = {
-                    "order": format_order(order, M), "comm_points": amount,
-                    "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
-                    "pass_ms": [round(v, 4) for v in pass_ms]}
+                name = f"{'x'.join(map(str, shape))} P={P} {'worst' if want else 'best'}"
+                out[name] = {"order": format_order(order, M), "comm_points": amount,
+                             "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
+                             "pass_ms": [round(v, 4) for v in pass_ms],
+                             "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name), B)}
     return out
+
+
+# ncu summaries of single-volume launches of the 4-D / 5-D configurations
+MD_PROFILES = {"64x64x64x64 P=64 best": os.path.join(ROOT, "profiles", "fft_pass_64x4_c64.md"),
+               "24x24x24x24x24 P=64 best": os.path.join(ROOT, "profiles", "fft_pass_24x5_c64.md")}
+
+
+def pass_roofline(launch_bytes, pass_ms, profile=None, volumes=1):
+    """HBM roofline of every pass of a configuration: algorithmic bytes of a
+    launch (read + write of the array) over its CUDA-event time, the fraction
+    of the measured copy peak, and, when a committed ncu summary of the same
+    kernels holds the DRAM traffic of each pass (one volume per launch), that
+    traffic scaled to the launch over the algorithmic bytes."""
+    peak, kind = peaks()
+    ach = [launch_bytes / (t * 1e-3) / 1e9 for t in pass_ms]
+    r = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": kind,
+         "algorithmic_bytes_per_launch": launch_bytes,
+         "achieved_per_pass": [round(a, 1) for a in ach], "frac_per_pass": [round(a / peak, 4) for a in ach],
+         "frac": round(launch_bytes * len(pass_ms) / (sum(pass_ms) * 1e-3) / 1e9 / peak, 4)}
+    if profile:
+        vals = profile_values(profile)
+        tr = [vals.get(f"traffic_bytes_pass_{s_}") for s_ in range(len(pass_ms))]
+        if all(t is not None for t in tr):
+            r["traffic_per_pass"] = [t * volumes for t in tr]
+            r["traffic_over_algorithmic"] = [round(t * volumes / launch_bytes, 3) for t in tr]
+    return r
 
 
 def decomposition_study(dev):
@@ -656,43 +761,67 @@ def decomposition_study(dev):
     return out
 
 
-def precision_study(dev):
-    """512^3, N(0,1) re/im: FP32 SIMT vs tensor-core FP16 / BF16 hi-lo passes.
-    Throughput of the forward transform and its relative L2 error against the
-    complex128 (FP64) GPU path, which the parity tests tie to the CPU oracle."""
+PRECISION_PROFILES = {"c64": os.path.join(ROOT, "profiles", "fft_pass_512cubed_c64.md"),
+                      "c64_tc_fp16": os.path.join(ROOT, "profiles", "fft_pass_512cubed_tc_fp16.md")}
+PRECISION_BOUNDS = {"c64": 1e-5, "c64_tc_fp16": 1e-5, "c64_tc_bf16": 1e-4, "c128": 1e-12}
+
+
+def precision_study(dev, with_oracle=True):
+    """512^3, N(0,1) re/im (seed 1306), P = 4096, the planner's best order:
+    forward transform of the FP32 SIMT path, the tensor-core FP16 / BF16
+    hi-lo paths and the FP64 path.  Throughput (bytes of the M passes) and,
+    with_oracle, every output element against the FP64 oracle's spectrum of
+    the same input: rel-L2 and the largest element error over the RMS, beside
+    the stated bound."""
     import numpy as np
     import torch
 
     import synth_inputs as si
-    from paper_1302_6189_gb300 import Plan, format_order
+    from paper_1302_6189_gb300 import Plan, format_order, mdfft_order_search
 
     shape = (512, 512, 512)
     per_transform, T = algorithmic_bytes(shape, 8)
-    x = torch.from_numpy(si.gaussian_complex(shape, si.SEEDS["precision512"], np.complex64)).to(dev)
-    with Plan(shape, 4096, None, "c128") as pl:
-        ref = pl.exec(x.to(torch.complex128))
-        order = pl.order()
-    out = {"order": format_order(order, 3), "reference": "complex128 GPU path", "dtypes": {}}
-    y = torch.empty_like(x)
-    for dt in ("c64", "c64_tc_fp16", "c64_tc_bf16"):
+    xh = si.gaussian_complex(shape, si.SEEDS["precision512"], np.complex64)
+    x = torch.from_numpy(xh).to(dev)
+    order, _ = mdfft_order_search(shape, 4096, 0)
+    out = {"order": format_order(order, 3), "reference": "FP64 oracle (CPU), every element" if with_oracle
+           else "none (run without the CPU oracle)", "dtypes": {}}
+    ref = None
+    if with_oracle:
+        ref, secs = oracle_spectrum(xh, len(os.sched_getaffinity(0)))
+        out["oracle_seconds"] = round(secs, 3)
+    for dt in ("c64", "c64_tc_fp16", "c64_tc_bf16", "c128"):
+        xin = x.to(torch.complex128) if dt == "c128" else x
+        y = torch.empty_like(xin)
         with Plan(shape, 4096, order, dt) as pl:
             for _ in range(2):
-                pl.exec(x, y)
+                pl.exec(xin, y)
+            pl.set_timing(True)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             for _ in range(5):
-                pl.exec(x, y)
+                pl.exec(xin, y)
             b.record()
             torch.cuda.synchronize(dev)
+            pl.check()
             ms = a.elapsed_time(b) / 5
-            err = float((torch.linalg.vector_norm(y.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref)).item())
-        out["dtypes"][dt] = {"gbs": round(per_transform / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4),
-                             "rel_l2_vs_fp64": err}
-    del ref
+            pass_ms, _ = pl.pass_times()
+        elem = 16 if dt == "c128" else 8
+        row = {"gbs": round(per_transform * elem / 8 / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4),
+               "pass_ms": [round(v, 4) for v in pass_ms], "bound_rel_l2": PRECISION_BOUNDS[dt]}
+        if dt != "c128":  # the complex128 path is FP64-bound (see extra.c128)
+            row["roofline"] = pass_roofline(2 * T * elem, pass_ms, PRECISION_PROFILES.get(dt))
+        if ref is not None:
+            row.update(errors_vs(y.cpu().numpy(), ref))
+            row["within_bound"] = row["rel_l2"] <= PRECISION_BOUNDS[dt]
+        out["dtypes"][dt] = row
+        del xin, y
     return out
 
 
 def profile_case(args):
+    """Two forward transforms of a batch of volumes with the planner's best
+    order (M + M pass launches: a warm-up, then the profiled ones)."""
     import numpy as np
     import torch
 
@@ -700,19 +829,21 @@ def profile_case(args):
     from paper_1302_6189_gb300 import Plan
 
     torch.cuda.set_device(0)
+    shape = tuple(int(v) for v in args.profile_shape.split(","))
     npdt = np.complex128 if args.profile_dtype == "c128" else np.complex64
     B = args.profile_batch
-    x = torch.empty((B,) + SHAPE if B > 1 else SHAPE, dtype=torch.from_numpy(np.zeros(1, npdt)).dtype,
+    x = torch.empty((B,) + shape if B > 1 else shape, dtype=torch.from_numpy(np.zeros(1, npdt)).dtype,
                     device="cuda")
     for i in range(B):
-        (x[i] if B > 1 else x).copy_(torch.from_numpy(si.uniform_complex(SHAPE, si.SEEDS["cube256"] + i, npdt)))
-    with Plan(SHAPE, args.P, None, args.profile_dtype, batch=B) as plan:
+        (x[i] if B > 1 else x).copy_(torch.from_numpy(si.uniform_complex(shape, si.SEEDS["cube256"] + i, npdt)))
+    with Plan(shape, args.P, None, args.profile_dtype, batch=B) as plan:
         y = torch.empty_like(x)
-        plan.exec(x, y)  # warm-up: launches 1-3
-        plan.exec(x, y)  # profiled: launches 4-6
+        plan.exec(x, y)  # warm-up: launches 1..M
+        plan.exec(x, y)  # profiled: launches M+1..2M
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": f"{B} x 256^3 {args.profile_dtype} forward", "order": plan.order_str(),
-                          "passes": plan.describe()}))
+        plan.check()
+        print(json.dumps({"profile_case": f"{B} x {'x'.join(map(str, shape))} {args.profile_dtype} forward",
+                          "order": plan.order_str(), "passes": plan.describe()}))
 
 
 def serving_study(dev, n=2000, budget=40e9):

@@ -310,8 +310,9 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * the next axis), `reps` launches each, and keeps the fastest.  For even
  * complex64 lengths up to 512 the candidates include a persistent kernel
  * that streams tiles through shared memory with bulk (TMA) copies; a plan
- * using it needs 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).  Tiling never
- * changes results.  in_dev (T elements, only read) and out_dev (T elements,
+ * using it needs 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).
+ * Tensor-core plans (lengths 128, 256, 512) also try 128-thread CTAs (half
+ * the lines per tile, more CTAs per SM).  Tiling never changes results.  in_dev (T elements, only read) and out_dev (T elements,
  * overwritten with scratch) are the caller's; the call synchronises `stream`.
  * ms_before / ms_after (M entries each, may be NULL) receive the mean pass
  * times of the default and of the chosen configuration.
@@ -320,7 +321,8 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * mdfft_plan_tuning / mdfft_plan_set_tuning -- a plan's launch choices as 4
  * int32 per pass (kernel variant: 0 default, 1 fixed 256-thread CTAs, 2
  * fixed 512-thread CTAs, 3 / 4 persistent pipelined with 1 / 2 landing
- * buffers; lines per tile along g; lines per tile along h; 0), e.g. after
+ * buffers, 5 tensor-core kernel with 128-thread CTAs; lines per tile along
+ * g; lines per tile along h; 0), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,
  * order, dtype, batch and flags.  set_tuning checks every pass (variant built
  * for its length and dtype, tile within the kernel's lines and the pass's
@@ -345,6 +347,20 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *ou
  */
 mdfft_status mdfft_pattern_probe(mdfft_plan_t plan, int s, const void *in_dev, void *out_dev, int reps,
                                  mdfft_stream_t stream, float *ms);
+
+/*
+ * mdfft_fp64_rate_probe -- measures the device's FP64 multiply-add rate, the
+ * denominator of the complex128 path's ALU roofline (that path is bound by
+ * the FP64 pipe, not by HBM).  A kernel of `ctas` CTAs x 256 threads runs, in
+ * every thread, 8 independent chains of `iters` fused multiply-adds (no
+ * memory traffic inside the loop), timed with CUDA events on `stream`
+ * (synchronised); *tflops = 2 x (multiply-adds executed) / seconds / 1e12.
+ *   out_dev   caller-owned device array of ctas x 256 doubles; each thread
+ *             writes the sum of its chains there, so no chain is optimised away.
+ *   ctas      1 .. 2^20; iters 1 .. 2^24.
+ */
+mdfft_status mdfft_fp64_rate_probe(double *out_dev, int ctas, int64_t iters, mdfft_stream_t stream,
+                                   double *tflops);
 
 /* Waits for the device and reports whether a pass kernel of this plan gave up
  * a bounded wait since the last check (MDFFT_E_TIMEOUT; the affected output
@@ -456,7 +472,9 @@ mdfft_status mdfft_server_destroy(mdfft_server_t s);
  * device array of MDFFT_NOALLOC_SCRATCH_BYTES that every GPU which loads the
  * library holds until the process exits.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call on each device before any stream capture.
+ * first call on each device before any stream capture.  The cached address
+ * does not survive cudaDeviceReset: after resetting a device, do not call
+ * this entry point on it again in the same process.
  *   M, N, dt, dir, normalize  as for mdfft_plan / mdfft_exec.
  *   order     M*M axis ids as for mdfft_plan; required (NULL is E_ARG) --
  *             get the best order from mdfft_order_search beforehand.

@@ -141,7 +141,8 @@ constexpr int kTcSharedBytes = 4112;
 // the tensor-core variant (complex64 only): radix-16 stages run as GEMMs.
 // THR != 0 fixes the CTA at THR threads for every length (the persistent
 // serving kernel): a power-of-two number of threads per line and THR / that
-// many lines per tile (stage loops skip butterflies a thread does not own).
+// many lines per tile (stage loops skip butterflies a thread does not own);
+// for a tensor-core kernel THR / (N / 16) lines (one butterfly per thread).
 __host__ __device__ constexpr int pow2ceil(int x) {
     int p = 1;
     while (p < x) p *= 2;
@@ -165,7 +166,9 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int TL0 = N / plan.maxR;  // one butterfly per thread in the widest stage
     static constexpr int kMinLines = 128 / (int)sizeof(C);
     static constexpr bool POW2 = sizeof(Real) == 4 && TC == 0 && pow2_threads_default(N);
-    static constexpr int TL = THR    ? (pow2ceil(TL0) < THR / kMinLines ? pow2ceil(TL0) : THR / kMinLines)
+    // (tensor-core CTAs keep one radix-16 butterfly per thread: THR only sets their line count)
+    static constexpr int TL = TC     ? TL0
+                              : THR  ? (pow2ceil(TL0) < THR / kMinLines ? pow2ceil(TL0) : THR / kMinLines)
                               : POW2 ? pow2ceil(TL0)
                                      : TL0;
     static constexpr int kTileElems = sizeof(Real) == 4 ? 4096 : 2048;

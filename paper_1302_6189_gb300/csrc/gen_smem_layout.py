@@ -2,7 +2,7 @@
 """Writes smem_layout.h: shared-memory padding of the complex64 pass kernels.
 
 For every complex64 line length N (up to 256) and CTA variant (default, 256 or
-512 threads) this replays the kernel's shared-memory accesses -- staged tile
+512 threads; 192 or 384 for 24 and 48) this replays the kernel's shared-memory accesses -- staged tile
 loads, every Stockham stage's reads and writes, the transposed-tile writes of
 the last stage and the store role's reads -- warp instruction by warp
 instruction, counts the wavefronts each needs (8-byte accesses are served
@@ -133,15 +133,20 @@ def best(n, thr):
     return (c[2], c[3], c[4]) if c[0] < default else (16, 1, 1)
 
 
+THREE_LINES = [24, 48]  # fixed 192 / 384-thread variants (48 / 96 lines)
+
+
 def main():
     rows = []
-    for thr in (0, 256, 512):
+    for thr in (0, 256, 512, 192, 384):
         for n in LENGTHS + [512]:
             if thr == 0 and n > 256:
                 continue
-            if thr and n not in set(TUNED) | set(SERVE):
+            if thr in (256, 512) and n not in set(TUNED) | set(SERVE):
                 continue
             if thr == 512 and n not in TUNED:
+                continue
+            if thr in (192, 384) and n not in THREE_LINES:
                 continue
             if n < 2 or not radix_plan(n):
                 continue

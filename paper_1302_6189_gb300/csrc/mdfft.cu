@@ -140,6 +140,27 @@ void choose_tile(int lines, int64_t Ng, int64_t Nh, size_t elem, int *Bg, int *B
     }
 }
 
+// Small grids: shrinks the tile of a built pass (along h first, then along g
+// down to 128-byte store runs) until the pass fills about one resident wave of
+// CTAs; idle lanes in a CTA cost less than idle SMs.  Updates the tile counts
+// and ps.ctas (not the divisors); returns the wave.  No heap use.
+int64_t shrink_to_wave(Pass &ps, size_t elem, bool line_store) {
+    PassArgs &a = ps.args;
+    const int64_t rest = ps.ctas / (a.gblocks * a.hblocks);
+    const int64_t wave = mdfft::detail::wave_ctas(ps.k);
+    const int min_bg = std::max(1, (int)(128 / elem));
+    while (ps.ctas < wave && (a.Bh > 1 || (!line_store && a.Bg > min_bg))) {
+        if (a.Bh > 1)
+            a.Bh = (a.Bh + 1) / 2;
+        else
+            a.Bg = std::max(min_bg, (a.Bg + 1) / 2);
+        a.gblocks = (a.Ng + a.Bg - 1) / a.Bg;
+        a.hblocks = (a.Nh + a.Bh - 1) / a.Bh;
+        ps.ctas = a.gblocks * a.hblocks * rest;
+    }
+    return wave;
+}
+
 mdfft_status build_pass(mdfft_plan_s *p, int s) {
     const int M = p->M;
     const pl::Layout &L = p->order[s];
@@ -202,21 +223,7 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
         a.nrest++;
         ps.ctas *= p->batch;
     }
-    // small grids: shrink the tile (along h first, then along g down to
-    // 128-byte store runs) until the pass fills about one resident wave of
-    // CTAs; idle lanes in a CTA cost less than idle SMs
-    const int64_t rest = ps.ctas / (a.gblocks * a.hblocks);
-    const int64_t wave = mdfft::detail::wave_ctas(ps.k);
-    const int min_bg = std::max(1, (int)(128 / p->elem));
-    while (ps.ctas < wave && (a.Bh > 1 || (!line_store && a.Bg > min_bg))) {
-        if (a.Bh > 1)
-            a.Bh = (a.Bh + 1) / 2;
-        else
-            a.Bg = std::max(min_bg, (a.Bg + 1) / 2);
-        a.gblocks = (Ng + a.Bg - 1) / a.Bg;
-        a.hblocks = (Nh + a.Bh - 1) / a.Bh;
-        ps.ctas = a.gblocks * a.hblocks * rest;
-    }
+    const int64_t wave = shrink_to_wave(ps, p->elem, line_store);
     set_tile_divisors(a, ps.ctas);
     a.own_in = owner_map(M, p->N, p->P, L);
     a.own_out = owner_map(M, p->N, p->P, Lo);
@@ -906,12 +913,16 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
         std::vector<PassKernel> variants{ps.k};
         PassKernel k;
         if (p->dt == MDFFT_C64) {
-            for (int thr : {256, 512})
+            for (int thr : {256, 512, 192, 384})
                 if (mdfft::find_pass_kernel_c64_thr(ps.n, thr, &k) && k.threads != ps.k.threads) variants.push_back(k);
             for (int nbuf : {1, 2})
                 if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && (uintptr_t)in % 16 == 0 &&
                     (uintptr_t)out % 16 == 0)
                     variants.push_back(k);
+        }
+        if (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) {
+            const int tc = p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16;
+            if (mdfft::find_pass_kernel_tc_thr(ps.n, tc, 128, &k) && k.fn != ps.k.fn) variants.push_back(k);
         }
         float best_ms = -1.f, default_ms = -1.f;
         Pass best = ps;
@@ -985,10 +996,19 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
 namespace {
 
 // The launch variants the autotuner chooses among, by code:
-// 0 default, 1 / 2 fixed 256 / 512-thread CTAs, 3 / 4 pipelined with 1 / 2 landing buffers.
+// 0 default, 1 / 2 fixed 256 / 512-thread CTAs, 3 / 4 pipelined with 1 / 2 landing buffers,
+// 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 / 384-thread CTAs.
+constexpr int kTuningVariants = 8;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     switch (variant) {
+        case 6:
+        case 7:
+            return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_thr(n, variant == 6 ? 192 : 384, k);
+        case 5:
+            return (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) &&
+                   mdfft::find_pass_kernel_tc_thr(n, p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16,
+                                                  128, k);
         case 0:
             return lookup(p->dt, n, k);
         case 1:
@@ -1011,7 +1031,7 @@ mdfft_status mdfft_plan_tuning(mdfft_plan_t p, int32_t *out, int cap) {
     for (int s = 0; s < p->M; ++s) {
         const Pass &ps = p->pass[s];
         int variant = -1;
-        for (int v = 0; v <= 4 && variant < 0; ++v) {
+        for (int v = 0; v < kTuningVariants && variant < 0; ++v) {
             PassKernel k;
             if (tuning_kernel(p, s, v, &k) && k.fn == ps.k.fn) variant = v;
         }
@@ -1031,7 +1051,7 @@ mdfft_status mdfft_plan_set_tuning(mdfft_plan_t p, const int32_t *in, int n) {
         PassKernel k;
         const int variant = in[4 * s], Bg = in[4 * s + 1], Bh = in[4 * s + 2];
         if (!tuning_kernel(p, s, variant, &k)) return fail(MDFFT_E_ARG, "kernel variant not built for this pass");
-        if (k.persistent && k.lines != p->pass[s].k.lines)
+        if ((variant == 3 || variant == 4) && k.lines != p->pass[s].k.lines)
             return fail(MDFFT_E_ARG, "pipelined variant needs the default tile lines");
         PassArgs &a = cand.args;
         if (Bg < 1 || Bh < 1 || (int64_t)Bg * Bh > k.lines || Bg > a.Ng || Bh > a.Nh)
@@ -1150,7 +1170,10 @@ mdfft_status mdfft_destroy(mdfft_plan_t p) {
 // through) is this file-scope device array.  Every GPU that loads the library
 // holds it until the process exits.  Host code must not use the symbol's
 // address directly (on the host it names a stand-in); the device address is
-// taken once per device with cudaGetSymbolAddress and cached.
+// taken once per device with cudaGetSymbolAddress and cached.  The cache
+// does not survive cudaDeviceReset (the module is loaded again and the array
+// may move): a process that resets a device must not call this entry point
+// on that device afterwards.
 // ---------------------------------------------------------------------------
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MDFFT_NOALLOC_SCRATCH_BYTES];
@@ -1186,8 +1209,8 @@ mdfft_status noalloc_scratch(unsigned char **out) {
 }
 
 // Pass s of the order held in the fixed-size array L (no heap use): the same
-// launch configuration mdfft_plan builds, without the owner maps of the
-// count mode.
+// launch configuration mdfft_plan builds (tile shape, small-grid shrink),
+// without the owner maps of the count mode.
 mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dtype dt, size_t elem, int s,
                           Pass &ps) {
     pl::Layout nat;
@@ -1231,6 +1254,7 @@ mdfft_status noalloc_pass(int M, const int64_t *N, const pl::Layout *L, mdfft_dt
         a.nrest++;
         ps.ctas *= N[ax];
     }
+    shrink_to_wave(ps, elem, false);  // the small-grid tiles of mdfft_plan
     set_tile_divisors(a, ps.ctas);
     a.scale = 1.0;
     a.scaled = 0;

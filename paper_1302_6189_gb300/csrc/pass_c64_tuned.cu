@@ -1,6 +1,8 @@
 // pass_c64_tuned.cu -- complex64 pass kernels with a fixed CTA size (256 or 512
-// threads) for the common line lengths: the autotuner's alternatives to the
-// default launch shape of pass_c64.cu.
+// threads) for the common line lengths, and 192 or 384 threads (48 or 96
+// lines of 4 threads) for 24 and 48: the autotuner's alternatives to the
+// default launch shape of pass_c64.cu.  (48 and 96 lines tile axes whose
+// extent is a multiple of 3, e.g. 24 x 2 lines, without idle lines.)
 #include "passes.h"
 
 namespace mdfft {
@@ -12,6 +14,18 @@ template <int N, int THR> static PassKernel make_c64_thr() {
 }
 
 bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k) {
+    if (thr == 192 || thr == 384) {
+        switch (n) {
+#define MDFFT_CASE(N)                                                      \
+    case N:                                                                \
+        *k = thr == 192 ? make_c64_thr<N, 192>() : make_c64_thr<N, 384>(); \
+        return true;
+            MDFFT_CASE(24) MDFFT_CASE(48)
+#undef MDFFT_CASE
+            default:
+                return false;
+        }
+    }
     if (thr != 256 && thr != 512) return false;
     switch (n) {
 #define MDFFT_CASE(N)                                                           \

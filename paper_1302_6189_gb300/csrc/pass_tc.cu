@@ -5,10 +5,10 @@
 
 namespace mdfft {
 
-template <int N, int TC> static PassKernel make_tc() {
-    using Cfg = PassCfg<float, N, TC>;
-    PassKernel k{(const void *)&fft_pass_tc_kernel<N, TC>, Cfg::THREADS, Cfg::LINES, Cfg::TL, TcPassCfg<N, TC>::SMEM,
-                 Cfg::plan};
+template <int N, int TC, int THR = 0> static PassKernel make_tc() {
+    using Cfg = PassCfg<float, N, TC, THR>;
+    PassKernel k{(const void *)&fft_pass_tc_kernel<N, TC, THR>, Cfg::THREADS, Cfg::LINES, Cfg::TL,
+                 TcPassCfg<N, TC, THR>::SMEM, Cfg::plan};
     k.persistent = 1;
     k.bulk = 1;
     return k;
@@ -22,6 +22,22 @@ bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k) {
         *k = tc == kTcFp16 ? make_tc<N, kTcFp16>() : make_tc<N, kTcBf16>(); \
         return true;
         MDFFT_TC_LENGTHS(MDFFT_CASE)
+#undef MDFFT_CASE
+        default:
+            return false;
+    }
+}
+
+// 128-thread tensor-core CTAs (half the lines per tile, twice the CTAs per SM),
+// an autotuning variant for the lengths of the precision and 256^3 configurations
+bool find_pass_kernel_tc_thr(int64_t n, int tc, int thr, PassKernel *k) {
+    if ((tc != kTcFp16 && tc != kTcBf16) || thr != 128) return false;
+    switch (n) {
+#define MDFFT_CASE(N)                                                                      \
+    case N:                                                                                \
+        *k = tc == kTcFp16 ? make_tc<N, kTcFp16, 128>() : make_tc<N, kTcBf16, 128>(); \
+        return true;
+        MDFFT_CASE(128) MDFFT_CASE(256) MDFFT_CASE(512)
 #undef MDFFT_CASE
         default:
             return false;

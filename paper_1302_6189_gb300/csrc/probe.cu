@@ -1,4 +1,5 @@
-// probe.cu -- data movement of a pass without the FFT (mdfft_pattern_probe).
+// probe.cu -- data movement of a pass without the FFT (mdfft_pattern_probe),
+// and the device's FP64 multiply-add rate (mdfft_fp64_rate_probe).
 //
 // The same tile as the pass kernel with the butterflies left out: each line
 // is read into registers exactly as the first stage reads it (every thread
@@ -6,7 +7,7 @@
 // the transposed tile, and written by the same store role.  It moves exactly
 // the bytes of a pass in the same pattern, so its speed is the bound that
 // pattern puts on the pass.
-#include "passes.h"
+#include "plan_internal.h"
 
 namespace mdfft {
 
@@ -65,3 +66,51 @@ bool find_move_kernel_c64(int64_t n, PassKernel *k) {
 }
 
 }  // namespace mdfft
+
+namespace {
+
+// 8 independent multiply-add chains per thread: enough independent work per
+// warp to keep the FP64 pipe busy whatever its latency.
+__global__ void __launch_bounds__(256) dfma_rate_kernel(double *out, int64_t iters) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double m = 0.999999999, c = 1e-9 * (double)(threadIdx.x & 7);
+    double v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 1.0 + 1e-3 * (double)i + 1e-12 * (double)gid;
+    for (int64_t it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = fma(v[i], m, c);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += v[i];
+    out[gid] = s;
+}
+
+}  // namespace
+
+extern "C" mdfft_status mdfft_fp64_rate_probe(double *out, int ctas, int64_t iters, mdfft_stream_t stream,
+                                              double *tflops) {
+    if (!out || !tflops) return mdfft::detail::fail(MDFFT_E_ARG, "null argument");
+    if (ctas < 1 || ctas > (1 << 20) || iters < 1 || iters > (1 << 24))
+        return mdfft::detail::fail(MDFFT_E_ARG, "ctas must be in [1, 2^20] and iters in [1, 2^24]");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return mdfft::detail::fail(MDFFT_E_CUDA, "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return mdfft::detail::fail(MDFFT_E_CUDA, "cudaEventCreate");
+    }
+    dfma_rate_kernel<<<ctas, 256, 0, st>>>(out, iters < 64 ? iters : 64);  // warm-up
+    cudaEventRecord(e0, st);
+    dfma_rate_kernel<<<ctas, 256, 0, st>>>(out, iters);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return mdfft::detail::cuda_fail(e, "FP64 rate probe");
+    *tflops = 2.0 * 8.0 * 256.0 * (double)ctas * (double)iters / ((double)ms * 1e-3) / 1e12;
+    return MDFFT_OK;
+}

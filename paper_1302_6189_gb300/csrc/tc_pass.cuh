@@ -30,8 +30,8 @@ __host__ __device__ constexpr int tc_stage_count(const RadixPlan &p) {
     return c;
 }
 
-template <int N, int TC> struct TcPassCfg {
-    using Cfg = PassCfg<float, N, TC>;
+template <int N, int TC, int THR = 0> struct TcPassCfg {
+    using Cfg = PassCfg<float, N, TC, THR>;
     static constexpr int LAND = Cfg::LINES * N;  // complex64 per landing buffer
     static constexpr size_t HEAD = 128;          // the landing buffer's mbarrier, padded
     // + a second set of line offsets and tile coordinates (the next tile's are
@@ -45,18 +45,22 @@ template <int N, int TC> struct TcPassCfg {
     // shared memory per SM (228 KiB, 1 KiB of it reserved per CTA) and per CTA (227 KiB)
     static constexpr int MAX_RESIDENT = (int)(233472 / (SMEM + 1024));
     static_assert(SMEM <= 232448, "tile does not fit one CTA's shared memory");
-    // the TMEM columns of all CTAs that can share an SM fit its 512 columns, so
-    // tcgen05.alloc never waits on another CTA
+    // the TMEM columns of all CTAs of one launch that can share an SM fit its
+    // 512 columns, so within one launch tcgen05.alloc never waits.  Tensor-core
+    // kernels of different launches running at once (two plans on two
+    // streams) can share an SM; a CTA's tcgen05.alloc then waits until the
+    // other kernel's CTAs on that SM free their columns at their end (a
+    // stall, not a deadlock: no CTA waits on another kernel)
     static_assert(TcGeom<Cfg::THREADS>::COLS * MAX_RESIDENT <= 512, "TMEM columns of the resident CTAs");
 };
 
-template <int N, int TC>
-__global__ void __launch_bounds__(PassCfg<float, N, TC>::THREADS, TcPassCfg<N, TC>::MIN_BLOCKS)
+template <int N, int TC, int THR = 0>
+__global__ void __launch_bounds__(PassCfg<float, N, TC, THR>::THREADS, TcPassCfg<N, TC, THR>::MIN_BLOCKS)
     fft_pass_tc_kernel(const PassArgs a) {
-    using Cfg = PassCfg<float, N, TC>;
-    using P = TcPassCfg<N, TC>;
+    using Cfg = PassCfg<float, N, TC, THR>;
+    using P = TcPassCfg<N, TC, THR>;
     using C = float2;
-    using St = Stages<float, N, 0, 1, TC>;
+    using St = Stages<float, N, 0, 1, TC, THR>;
     static_assert(N % 2 == 0, "bulk copies need lines of whole 16-byte units");
     constexpr uint32_t kParStep = tc_stage_count(Cfg::plan) & 1;  // MMA mbarrier phases per tile, mod 2
     extern __shared__ __align__(128) unsigned char tc_smem[];
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(PassCfg<float, N, TC>::THREADS, TcPassCfg<N, T
             if (tid < 32 && t + G < a.ntiles) mbar_wait_bounded(lbar, lpar ^ 1, kTcWaitNs);
             break;
         }
-        store_tile<float, N, TC, 0>(a, buf, lbase, c, tid);
+        store_tile<float, N, TC, THR>(a, buf, lbase, c, tid);
         par ^= kParStep;
         // no barrier: the next tile's coordinates go to the other set, and its
         // first stage writes the tile region only after the next loop-top barrier

@@ -82,6 +82,7 @@ SIGNATURES = {
     "mdfft_plan_check": (c_int, [c_void_p]),
     "mdfft_pattern_probe": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, P_(ctypes.c_float)]),
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
+    "mdfft_fp64_rate_probe": (c_int, [c_void_p, c_int, i64, c_void_p, P_(ctypes.c_double)]),
     "mdfft_supported_length": (c_int, [i64, c_int]),
     "mdfft_destroy": (c_int, [c_void_p]),
     "mdfft_exec_noalloc": (c_int, [c_int, P_(i64), P_(c_int), c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -188,7 +189,7 @@ def mdfft_selftest_wait(arrive, limit_us):
     return st, waited.value
 
 
-TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2")
+TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384")
 
 
 def mdfft_plan_tuning(plan, M):
@@ -301,6 +302,14 @@ def mdfft_pattern_probe(plan, s, in_ptr, out_ptr, reps, stream):
     _check(_lib.mdfft_pattern_probe(plan, int(s), c_void_p(in_ptr), c_void_p(out_ptr), int(reps), c_void_p(stream),
                                     ctypes.byref(ms)), "mdfft_pattern_probe")
     return ms.value
+
+
+def mdfft_fp64_rate_probe(out_ptr, ctas, iters, stream):
+    """Measured FP64 multiply-add rate of the device, TFLOP/s (out_ptr: ctas x 256 doubles)."""
+    tf = ctypes.c_double()
+    _check(_lib.mdfft_fp64_rate_probe(c_void_p(out_ptr), int(ctas), int(iters), c_void_p(stream),
+                                      ctypes.byref(tf)), "mdfft_fp64_rate_probe")
+    return tf.value
 
 
 def mdfft_plan_check(plan):

@@ -165,3 +165,39 @@ def test_tile_dealing_does_not_change_results(chunk):
             srv.set_chunk(0)
     for sh, x, y in zip(shapes, xs, outs):
         assert torch.equal(y, alone(sh, x, -1, False))
+
+
+def test_serving_bench_lengths_mix_equals_alone_and_oracle():
+    # the lengths of the serving benchmark (3-D axes from {48, 64, 96, 128,
+    # 160, 192}, 4-D 32^4): every length in every axis position, plus a draw
+    # of the benchmark's own request generator, submitted while earlier
+    # requests are in flight
+    L = si.SERVING_AXES
+    shapes = [(L[i], L[(i + 1) % 6], L[(i + 3) % 6]) for i in range(6)] + [(32, 32, 32, 32)]
+    shapes += si.serving_requests(24, si.SEEDS["serving"])
+    rng = np.random.default_rng(17)
+    xs = [torch.from_numpy(si.uniform_complex(s, 1700 + i, np.complex64)).to(DEV) for i, s in enumerate(shapes)]
+    outs = [torch.empty_like(x) for x in xs]
+    dirs = [int(rng.choice([-1, 1])) for _ in shapes]
+    with md.Server(budget_bytes=8 << 30, max_inflight=16, P=64) as srv:
+        ids, i = [], 0
+        while i < len(shapes):
+            for _ in range(int(rng.integers(1, 5))):
+                if i < len(shapes):
+                    ids.append(srv.submit(xs[i], outs[i], dir=dirs[i], normalize=dirs[i] == 1))
+                    i += 1
+            srv.step()
+        srv.drain()
+        assert srv.stats()["completed"] == len(shapes)
+        for rid in ids:
+            assert srv.poll(rid)[0]
+            srv.release(rid)
+    torch.cuda.synchronize()
+    for s, x, y, d in zip(shapes, xs, outs, dirs):
+        assert torch.equal(y, alone(s, x, d, d == 1)), s
+    for k in list(range(7)) + list(range(7, len(shapes), 6)):  # every length, and a sample of the draw
+        ref = oracle.fftn(xs[k].cpu().numpy().astype(np.complex128), sign=dirs[k], nthreads=8)
+        if dirs[k] == 1:
+            ref = ref / ref.size
+        y = outs[k].cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= 1e-5, shapes[k]

@@ -52,3 +52,34 @@ def test_invalid_tuning_is_refused_whole():
             pl.set_tuning(bad)
         assert pl.tuning() == before  # nothing applied
         assert torch.equal(pl.exec(x), want)
+
+
+@pytest.mark.parametrize("shape,P,dt", [((24, 24, 24, 24), 64, "c64"), ((48, 24, 48), 16, "c64"),
+                                        ((64, 48, 256), 16, "c64_tc_fp16"), ((512, 16, 8), 16, "c64_tc_bf16")])
+def test_every_tuning_variant_gives_the_default_bits(shape, P, dt):
+    # each kernel variant the autotuner may choose for these lengths (fixed
+    # 192 / 384 / 256 / 512-thread CTAs; 128-thread tensor-core CTAs), set on
+    # every pass where it is built, reproduces the default plan's spectrum
+    x = torch.from_numpy(si.uniform_complex(shape, 970, np.complex64)).to(DEV)
+    with md.Plan(shape, P, None, dt) as pl:
+        want = pl.exec(x)
+        base = pl.tuning()
+        tried = 0
+        for v in md.mdfft.TUNING_VARIANTS[1:]:
+            if v.startswith("pipe"):
+                continue
+            for s in range(len(shape)):
+                t = [dict(d) for d in base]
+                t[s]["variant"], t[s]["tile_g"], t[s]["tile_h"] = v, 1, 1
+                try:
+                    pl.set_tuning(t)
+                except md.MdfftError:
+                    continue  # not built for this length
+                d = pl.describe()[s]
+                tried += 1
+                assert torch.equal(pl.exec(x), want), (v, s, d)
+        pl.set_tuning(base)
+        assert tried >= 1
+        y = torch.empty_like(x)
+        pl.autotune(x, y, reps=2)
+        assert torch.equal(pl.exec(x), want)

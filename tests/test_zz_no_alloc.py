@@ -65,3 +65,24 @@ def test_noalloc_rejects_arrays_beyond_its_scratch():
     with pytest.raises(md.MdfftError) as e:
         md.mdfft_exec_noalloc((8, 8, 8), None, "c64", x.data_ptr(), x.data_ptr(), -1, 0, 0)
     assert e.value.status == md.mdfft.MDFFT_E_ARG
+
+
+def test_noalloc_allocates_no_device_memory():
+    # after one warm-up call (kernels loaded, the scratch address looked up),
+    # further calls change neither torch's allocator nor the device's free memory
+    shape, order, dt, seed = CASES[0]
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    x = torch.from_numpy(si.uniform_complex(shape, 420, NP[dt])).to(DEV)
+    y = torch.empty_like(x)
+    md.mdfft_exec_noalloc(shape, order, dt, x.data_ptr(), y.data_ptr(), -1, 0, stream)
+    torch.cuda.synchronize(DEV)
+    first = y.clone()
+    torch.cuda.synchronize(DEV)
+    torch_before = torch.cuda.memory_allocated(DEV)
+    free_before = torch.cuda.mem_get_info(DEV)[0]
+    for _ in range(4):
+        md.mdfft_exec_noalloc(shape, order, dt, x.data_ptr(), y.data_ptr(), -1, 0, stream)
+    torch.cuda.synchronize(DEV)
+    assert torch.cuda.memory_allocated(DEV) == torch_before
+    assert torch.cuda.mem_get_info(DEV)[0] == free_before
+    assert torch.equal(y, first)  # the same bits on every call
