@@ -392,7 +392,7 @@ def run_ours(args):
     import torch
 
     import synth_inputs as si
-    from paper_1302_6189_gb300 import Plan, format_order, mdfft_order_search
+    from paper_1302_6189_gb300 import MDFFT_PLAN_TUNE_RADIX, Plan, format_order, mdfft_order_search
 
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
@@ -401,7 +401,8 @@ def run_ours(args):
     per_transform, T = algorithmic_bytes(shape, elem)
     order, total_amount = mdfft_order_search(shape, P, 0)
     # one batched plan: every pass is one launch over the tiles of all B volumes
-    plan = Plan(shape, P, order, "c64", batch=B)
+    # (the autotuner may also pick another radix split of the line length)
+    plan = Plan(shape, P, order, "c64", MDFFT_PLAN_TUNE_RADIX, batch=B)
     comm = plan.comm_volume()
 
     xs = torch.empty((B,) + shape, dtype=torch.complex64, device=dev)
@@ -414,7 +415,7 @@ def run_ours(args):
     nvtx.range_push("autotune")
     tune_before, tune_after = plan.autotune(xs, ys, reps=5)
     nvtx.range_pop()
-    tuned = [{k: d[k] for k in ("threads", "tile_g", "tile_h", "ctas")} for d in plan.describe()]
+    tuned = [{k: d[k] for k in ("threads", "tile_g", "tile_h", "ctas", "radix", "tile_order")} for d in plan.describe()]
 
     def step():
         plan.exec(xs, ys, dir=-1)
@@ -611,12 +612,48 @@ def extra_table(dev, x, P, with_oracle=True):
                                 "dp_flops_per_launch_per_volume": counted,
                                 "achieved_nominal_5TlogT": round(fp64_tflops, 3),
                                 "frac_nominal_work": round(fp64_tflops / peak64, 3)}}
+    res["chunk_tile_order"] = chunk_order_study(dev, x, P)
     res["small_32cubed_c128"] = small_study(dev)
     res["precision_512cubed"] = precision_study(dev, with_oracle)
     res["md_4d_5d"] = md_study(dev)
     res["decompositions"] = decomposition_study(dev)
     res["serving"] = serving_study(dev)
     return res
+
+
+def chunk_order_study(dev, x, P, reps=10):
+    """The bench workload's forward passes in the two tile orders: tiles along
+    the output's fastest axis (default) and input-chunk order with one f_MD
+    chunk per tile (16 x 1 lines: CTA t owns chunk t of the input layout),
+    GB/s per pass, same kernel."""
+    import torch
+
+    from paper_1302_6189_gb300 import Plan, mdfft_order_search
+
+    B = x.shape[0]
+    _, T = algorithmic_bytes(SHAPE, 8)
+    order, _ = mdfft_order_search(SHAPE, P, 0)
+    y = torch.empty_like(x)
+    out = {"note": f"{B} volumes per launch, forward, {reps} reps, default kernel for both"}
+    with Plan(SHAPE, P, order, "c64", batch=B) as pl:
+        want = pl.exec(x).clone()
+        base = pl.tuning()
+        for name, tuning in (("output_runs", base),
+                             ("input_chunk_per_cta", [dict(t, tile_g=16, tile_h=1, tile_order=1) for t in base])):
+            pl.set_tuning(tuning)
+            for _ in range(2):
+                pl.exec(x, y)
+            pl.set_timing(True)
+            for _ in range(reps):
+                pl.exec(x, y)
+            torch.cuda.synchronize(dev)
+            pass_ms, _ = pl.pass_times()
+            pl.set_timing(False)
+            out[name] = {"gbs_per_pass": [round(2 * B * T * 8 / (m * 1e-3) / 1e9, 1) for m in pass_ms],
+                         "ctas": [d["ctas"] for d in pl.describe()], "store_axis": [d["store_axis"] for d in pl.describe()],
+                         "same_bits": bool(torch.equal(y, want))}
+        pl.set_tuning(base)
+    return out
 
 
 def small_study(dev, reps=2000):
@@ -662,7 +699,7 @@ def md_study(dev, reps=10):
     import torch
 
     import synth_inputs as si
-    from paper_1302_6189_gb300 import Plan, format_order, mdfft_order_search
+    from paper_1302_6189_gb300 import MDFFT_PLAN_TUNE_RADIX, Plan, format_order, mdfft_order_search
 
     out = {}
     for shape in ((64, 64, 64, 64), (24, 24, 24, 24, 24)):
@@ -675,8 +712,9 @@ def md_study(dev, reps=10):
         for P in (64, 1024):
             for want in (0, 1):
                 order, amount = mdfft_order_search(shape, P, want)
-                with Plan(shape, P, order, "c64", batch=B) as pl:
+                with Plan(shape, P, order, "c64", MDFFT_PLAN_TUNE_RADIX, batch=B) as pl:
                     pl.autotune(x, y, reps=3)
+                    tuning = [dict(t, radix=d["radix"]) for t, d in zip(pl.tuning(), pl.describe())]
                     for _ in range(3):
                         pl.exec(x, y)
                     pl.set_timing(True)
@@ -691,7 +729,7 @@ def md_study(dev, reps=10):
                 name = f"{'x'.join(map(str, shape))} P={P} {'worst' if want else 'best'}"
                 out[name] = {"order": format_order(order, M), "comm_points": amount,
                              "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
-                             "pass_ms": [round(v, 4) for v in pass_ms],
+                             "pass_ms": [round(v, 4) for v in pass_ms], "tuning": tuning,
                              "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name), B)}
     return out
 
@@ -939,12 +977,14 @@ def serving_study(dev, n=2000, budget=40e9):
         run_plain(zero)
         plain_sat = run_plain(zero)
         out = {"requests": n, "budget_gb": budget / 1e9, "grid_ctas_per_sm": best[1], "depth": best[2],
-               "chunk_tiles": best[3],
+               "chunk_tiles": best[3], "direct_max_requests": 4,
                "saturated": {"batched": summary(zero, sat), "plain": summary(zero, plain_sat)}, "poisson": {}}
         for frac in (0.5, 0.8, 1.0):
             arrivals = si.poisson_arrivals(n, frac * X, si.SEEDS["serving"])
             arrivals = arrivals - arrivals[0]
+            d0 = srv.stats()["direct_requests"]
             b = summary(arrivals, run_server(srv, arrivals))
+            b["direct_requests"] = srv.stats()["direct_requests"] - d0
             p = summary(arrivals, run_plain(arrivals))
             out["poisson"][f"{frac:.1f}X"] = {"rate_per_s": round(frac * X, 1), "batched": b, "plain": p}
         out["server_stats"] = srv.stats()

@@ -101,6 +101,10 @@ typedef enum {
 #define MDFFT_PLAN_DECOMP_SLAB 0x10u
 #define MDFFT_PLAN_DECOMP_PENCIL 0x20u
 #define MDFFT_PLAN_DECOMP_VOLUMETRIC 0x40u
+/* Lets mdfft_plan_autotune also choose among radix splits of a line length
+ * (radix_plan_alt, e.g. 8x8x4 for 256): the spectrum then changes in its
+ * rounding only.  Without it autotuning never changes a result bit. */
+#define MDFFT_PLAN_TUNE_RADIX 0x100u
 
 /*
  * mdfft_plan -- build a plan for the M-D FFT of dims N[0..M) with Np = P
@@ -289,16 +293,22 @@ mdfft_status mdfft_pass_times(mdfft_plan_t plan, float *ms_out, int cap, int *n_
 mdfft_status mdfft_exec_host(mdfft_plan_t plan, const void *in_host, void *out_host, void *dev_in, void *dev_out,
                              int dir, int normalize, mdfft_stream_t stream);
 
-/* Launch shape of pass s: line length, tile (lines along the output's
- * fastest axis x lines along the next axis), threads per CTA, CTAs, bytes of
- * shared memory.  Host information only. */
+/* Launch shape of pass s: line length, tile (lines along the tile axes g and
+ * h), threads per CTA, CTAs, bytes of shared memory, the radix plan of the
+ * 1-D FFTs and the tile order.  Host information only. */
 typedef struct {
     int64_t line_length;
     int tile_g, tile_h, threads, smem_bytes;
     int64_t ctas;      /* tiles */
-    int fft_axis, store_axis;
+    int fft_axis, store_axis;  /* store_axis: the tile axis g */
     int64_t grid;      /* CTAs launched (= ctas unless persistent) */
     int persistent;    /* 0: one CTA per tile; 1 or 2: persistent kernel with that many landing buffers */
+    int stages;        /* radix stages of the line length's plan */
+    int radix[12];     /* their radices, first stage first (e.g. 16, 16 for 256) */
+    int tile_order;    /* 0: g is the output layout's fastest axis (runs of tile_g elements stored);
+                          1: input-chunk order (g, h the input layout's second and third fastest axes,
+                          tiles in the input's row-major line order: a tile of whole f_MD chunks is one
+                          chunk, CTA t owning chunk t) */
 } mdfft_pass_info;
 mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out);
 
@@ -312,7 +322,12 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * that streams tiles through shared memory with bulk (TMA) copies; a plan
  * using it needs 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).
  * Tensor-core plans (lengths 128, 256, 512) also try 128-thread CTAs (half
- * the lines per tile, more CTAs per SM).  Tiling never changes results.  in_dev (T elements, only read) and out_dev (T elements,
+ * the lines per tile, more CTAs per SM), and non-persistent kernels the
+ * input-chunk tile order (mdfft_pass_info.tile_order).  Plans made with
+ * MDFFT_PLAN_TUNE_RADIX (complex64) also try the alternative radix plan of
+ * the length (its twiddle table is made again for the chosen plan).  Kernel
+ * variant, tiling and tile order never change results; a different radix
+ * plan changes the rounding only.  in_dev (T elements, only read) and out_dev (T elements,
  * overwritten with scratch) are the caller's; the call synchronises `stream`.
  * ms_before / ms_after (M entries each, may be NULL) receive the mean pass
  * times of the default and of the chosen configuration.
@@ -321,8 +336,11 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * mdfft_plan_tuning / mdfft_plan_set_tuning -- a plan's launch choices as 4
  * int32 per pass (kernel variant: 0 default, 1 fixed 256-thread CTAs, 2
  * fixed 512-thread CTAs, 3 / 4 persistent pipelined with 1 / 2 landing
- * buffers, 5 tensor-core kernel with 128-thread CTAs; lines per tile along
- * g; lines per tile along h; 0), e.g. after
+ * buffers, 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 /
+ * 384-thread CTAs (lengths 24, 48), 8 the alternative radix plan (lengths 32,
+ * 48, 64, 96, 128, 160, 192, 256, 512: e.g. 8x8x4 for 256, 8x8x8 for 512);
+ * lines per tile along g; lines per tile along h; tile order 0 or 1, see
+ * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,
  * order, dtype, batch and flags.  set_tuning checks every pass (variant built
  * for its length and dtype, tile within the kernel's lines and the pass's
@@ -393,7 +411,12 @@ mdfft_status mdfft_destroy(mdfft_plan_t plan);
  * next pass of every request in flight, whatever its shape.  A request that
  * arrives while others are on the GPU joins at the next step; it leaves after
  * its last pass.  Requests advance one pass per step, so a step has no
- * dependencies inside it and nothing waits on the device.  Line lengths
+ * dependencies inside it and nothing waits on the device.  At low load --
+ * no request queued and at most `direct` requests with passes left
+ * (mdfft_server_set_direct, default 4) -- a step instead launches every
+ * remaining pass of those requests, oldest first, as plain pass launches
+ * (those of mdfft_exec): a lone request then runs its passes back to back
+ * instead of one per step.  Line lengths
  * 16, 24, 32, 48, 64, 96, 128, 160, 192, 256 run inside the persistent
  * kernel; other supported lengths run as separate launches in the same step.
  * Results are the same as mdfft_exec's for the same shape (same kernels and
@@ -410,6 +433,7 @@ typedef struct {
     size_t bytes_in_use, budget_bytes;
     int grid_ctas; /* CTAs of the persistent kernel */
     int64_t cancelled;
+    int64_t direct_requests; /* requests whose remaining passes ran as plain launches (low load) */
 } mdfft_server_stats;
 
 /* budget_bytes: HBM admission budget; max_inflight: 1..512 requests in
@@ -455,6 +479,11 @@ mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth);
  * every CTA.  Larger chunks mean fewer item lookups, smaller ones evener
  * load.  Results do not depend on it. */
 mdfft_status mdfft_server_set_chunk(mdfft_server_t s, int chunk);
+/* Low-load threshold (0..64, default 4; 0 never): a step with no request
+ * queued and at most this many requests with passes left launches all their
+ * remaining passes directly, oldest request first.  Results do not depend on
+ * it. */
+mdfft_status mdfft_server_set_direct(mdfft_server_t s, int max_requests);
 mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out);
 mdfft_status mdfft_server_destroy(mdfft_server_t s);
 

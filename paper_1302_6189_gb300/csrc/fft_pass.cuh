@@ -75,7 +75,8 @@ struct PassArgs {
     int64_t Ng, Nh;                 // extents of g and h (ragged last tiles are masked)
     int64_t in_sg, in_sh;           // input strides of g and h
     int64_t out_sh, out_sf;         // output strides of h and f
-    int64_t out_sg;                 // output stride of g: 1, or N_f when the output keeps f fastest
+    int64_t out_sg;                 // output stride of g: 1 (g the output's fastest axis), N_f when the
+                                    // output keeps f fastest, or any stride (input-chunk tile order)
     int line_store;                 // 1: the output keeps f fastest (lines stored whole, no transpose)
     int conj;                       // inverse: bit 0 conjugates the loaded input, bit 1 the stored output
     double scale;                   // multiplies every stored value
@@ -111,6 +112,25 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
     while (n % 3 == 0) p.R[p.S++] = 3, n /= 3;
     for (int i = 0; i < p.S; ++i) p.maxR = p.R[i] > p.maxR ? p.R[i] : p.maxR;
     if (n != 1 || e > 10) p.S = -1;  // unsupported length
+    return p;
+}
+
+// The autotuner's alternative radix plan of a length: the power-of-two part
+// split otherwise (16 = 4x4, 32 = 16x2, 64 = 16x4, 128 = 8x4x4, 256 = 8x8x4,
+// 512 = 8x8x8, 1024 = 16x16x4; odd factors as in radix_plan).
+__host__ __device__ constexpr RadixPlan radix_plan_alt(int n) {
+    RadixPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, 1};
+    int e = 0;
+    while (n % 2 == 0) n /= 2, ++e;
+    const int pw[11][3] = {{0, 0, 0},  {2, 0, 0},  {4, 0, 0},  {8, 0, 0},  {4, 4, 0},  {16, 2, 0},
+                           {16, 4, 0}, {8, 4, 4}, {8, 8, 4}, {8, 8, 8}, {16, 16, 4}};
+    if (e <= 10)
+        for (int i = 0; i < 3; ++i)
+            if (pw[e][i]) p.R[p.S++] = pw[e][i];
+    while (n % 5 == 0) p.R[p.S++] = 5, n /= 5;
+    while (n % 3 == 0) p.R[p.S++] = 3, n /= 3;
+    for (int i = 0; i < p.S; ++i) p.maxR = p.R[i] > p.maxR ? p.R[i] : p.maxR;
+    if (n != 1 || e > 10) p.S = -1;
     return p;
 }
 
@@ -158,10 +178,12 @@ __host__ __device__ constexpr bool pow2_threads_default(int n) {
     return n == 24 || n == 48 || n == 240 || n == 480 || n == 960;
 }
 
-template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
+// RP = 1 selects the alternative radix plan (radix_plan_alt; SIMT kernels).
+template <typename Real, int N, int TC = 0, int THR = 0, int RP = 0> struct PassCfg {
     using C = typename Cx<Real>::T;
     static_assert(TC == 0 || sizeof(Real) == 4, "tensor-core stages are complex64 only");
-    static constexpr RadixPlan plan = TC ? radix_plan_tc(N) : radix_plan(N);
+    static_assert(RP == 0 || TC == 0, "alternative radix plans are SIMT only");
+    static constexpr RadixPlan plan = TC ? radix_plan_tc(N) : RP ? radix_plan_alt(N) : radix_plan(N);
     static_assert(plan.S >= 0, "unsupported line length");  // S = 0: N = 1, a pure redistribution
     static constexpr int TL0 = N / plan.maxR;  // one butterfly per thread in the widest stage
     static constexpr int kMinLines = 128 / (int)sizeof(C);
@@ -195,7 +217,7 @@ template <typename Real, int N, int TC = 0, int THR = 0> struct PassCfg {
     static constexpr int THREADS = TL * LINES;
     // shared-memory padding (the bank-conflict-free choice of smem_layout.h
     // for complex64; tensor-core and complex128 configurations use the default)
-    static constexpr SmemLayout LAY = (sizeof(Real) == 4 && TC == 0) ? smem_layout_c64(N, THR) : SmemLayout{16, 1, 1};
+    static constexpr SmemLayout LAY = (sizeof(Real) == 4 && TC == 0) ? smem_layout_c64(N, THR, RP) : SmemLayout{16, 1, 1};
     static constexpr int PADG = LAY.g;                // pad(i) = i + i / PADG
     static constexpr int PADN = N + N / PADG + LAY.pe;  // line stride of the stage buffer
     static constexpr int TROW = LINES + LAY.te;         // row of the transposed tile
@@ -348,8 +370,8 @@ __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
 // SRC selects where the first stage reads: -1 the default of the
 // configuration (HBM directly when DIRECT, else the staged tile), 2 a landing
 // buffer in shared memory holding the tile's lines unpadded (gsrc = the line).
-template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC = -1> struct Stages {
-    using Cfg = PassCfg<Real, N, TC, THR>;
+template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC = -1, int RP = 0> struct Stages {
+    using Cfg = PassCfg<Real, N, TC, THR, RP>;
     static constexpr int SRC0 = SRC >= 0 ? SRC : (Cfg::DIRECT ? 1 : 0);
     using C = typename Cfg::C;
     static constexpr int R = Cfg::plan.R[SI];
@@ -402,7 +424,7 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
             if constexpr (FIRST) after_first();
         }
         if constexpr (!LAST)
-            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC>::run(buf, tile, tw, gsrc, line, t, ok, conj, active,
+            Stages<Real, N, SI + 1, NS * R, TC, THR, SRC, RP>::run(buf, tile, tw, gsrc, line, t, ok, conj, active,
                                                                after_first, tc_par);
     }
 
@@ -521,10 +543,10 @@ __device__ __forceinline__ TileCoord tile_coords(const PassArgs &a, int64_t t) {
 // ...  so a warp writes runs of Bg consecutive elements.  Count mode adds the
 // points whose owner changes and the split-line amount (lbase: input offset
 // of every tile line).
-template <typename Real, int N, int TC, int THR>
-__device__ __forceinline__ void store_tile(const PassArgs &a, const typename PassCfg<Real, N, TC, THR>::C *buf,
+template <typename Real, int N, int TC, int THR, int RP = 0>
+__device__ __forceinline__ void store_tile(const PassArgs &a, const typename PassCfg<Real, N, TC, THR, RP>::C *buf,
                                            const int64_t *lbase, const TileCoord &c, const int tid) {
-    using Cfg = PassCfg<Real, N, TC, THR>;
+    using Cfg = PassCfg<Real, N, TC, THR, RP>;
     using C = typename Cfg::C;
     C *out = reinterpret_cast<C *>(a.out);
     const bool active = tid < Cfg::THREADS;
@@ -552,7 +574,7 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
             }
         }
     } else if (sok) {
-        const int64_t obase = c.out_base + sbh * a.out_sh + sbg;
+        const int64_t obase = c.out_base + sbh * a.out_sh + sbg * a.out_sg;
         C *op = out + obase + (int64_t)k0 * a.out_sf;
         const int64_t ostep = (int64_t)Cfg::TL * a.out_sf;
         const C *bp = buf + k0 * Cfg::TROW + sl;
@@ -593,9 +615,9 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
 // by several line lengths, see the grouped serving kernel) take part in the
 // barriers only.  (Tensor-core plans use the persistent kernel of
 // tc_pass.cuh instead.)
-template <typename Real, int N, int TC, int THR = 0>
+template <typename Real, int N, int TC, int THR = 0, int RP = 0>
 __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned char *smem_raw, const int tid) {
-    using Cfg = PassCfg<Real, N, TC, THR>;
+    using Cfg = PassCfg<Real, N, TC, THR, RP>;
     using C = typename Cfg::C;
     C *buf = reinterpret_cast<C *>(smem_raw);  // stage buffer [LINES][PADN] / transposed tile [N][TROW]
     C *tw = buf + Cfg::DATA;
@@ -648,17 +670,17 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
         __syncthreads();
     } else {
         const C *gsrc = in + lbase[line < Cfg::LINES ? line : 0];
-        Stages<Real, N, 0, 1, TC, THR>::run(buf, buf, tw, gsrc, line, tl, fok, (a.conj & 1) != 0, active);
+        Stages<Real, N, 0, 1, TC, THR, -1, RP>::run(buf, buf, tw, gsrc, line, tl, fok, (a.conj & 1) != 0, active);
     }
-    store_tile<Real, N, TC, THR>(a, buf, lbase, c, tid);
+    store_tile<Real, N, TC, THR, RP>(a, buf, lbase, c, tid);
 }
 
 // ------------------------------------------------------------------ the kernel
 
-template <typename Real, int N, int TC = 0, int THR = 0>
-__global__ void __launch_bounds__(PassCfg<Real, N, TC, THR>::THREADS) fft_pass_kernel(const PassArgs a) {
+template <typename Real, int N, int TC = 0, int THR = 0, int RP = 0>
+__global__ void __launch_bounds__(PassCfg<Real, N, TC, THR, RP>::THREADS) fft_pass_kernel(const PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pass_tile<Real, N, TC, THR>(a, blockIdx.x, smem_raw, threadIdx.x);
+    pass_tile<Real, N, TC, THR, RP>(a, blockIdx.x, smem_raw, threadIdx.x);
 }
 
 }  // namespace mdfft

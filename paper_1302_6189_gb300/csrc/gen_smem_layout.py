@@ -2,7 +2,8 @@
 """Writes smem_layout.h: shared-memory padding of the complex64 pass kernels.
 
 For every complex64 line length N (up to 256) and CTA variant (default, 256 or
-512 threads; 192 or 384 for 24 and 48) this replays the kernel's shared-memory accesses -- staged tile
+512 threads; 192 or 384 for 24 and 48; the alternative radix plan of the
+tuned lengths) this replays the kernel's shared-memory accesses -- staged tile
 loads, every Stockham stage's reads and writes, the transposed-tile writes of
 the last stage and the store role's reads -- warp instruction by warp
 instruction, counts the wavefronts each needs (8-byte accesses are served
@@ -25,13 +26,16 @@ POW2_DEFAULT = [24, 48, 240, 480, 960]  # pow2_threads_default() of fft_pass.cuh
 SERVE = [16, 24, 32, 48, 64, 96, 128, 160, 192, 256]
 
 
-def radix_plan(n):
+def radix_plan(n, rp=0):
     e = 0
     while n % 2 == 0:
         n //= 2
         e += 1
     pw = {0: [], 1: [2], 2: [4], 3: [8], 4: [16], 5: [8, 4], 6: [8, 8], 7: [16, 8], 8: [16, 16], 9: [16, 16, 2],
           10: [16, 8, 8]}
+    if rp:  # radix_plan_alt()
+        pw = {0: [], 1: [2], 2: [4], 3: [8], 4: [4, 4], 5: [16, 2], 6: [16, 4], 7: [8, 4, 4], 8: [8, 8, 4],
+              9: [8, 8, 8], 10: [16, 16, 4]}
     r = list(pw[e])
     while n % 5 == 0:
         r.append(5)
@@ -42,8 +46,8 @@ def radix_plan(n):
     return r
 
 
-def launch(n, thr, elem=8):
-    r = radix_plan(n)
+def launch(n, thr, elem=8, rp=0):
+    r = radix_plan(n, rp)
     tl0 = n // max(r) if r else n
     min_lines = 128 // elem
     p = 1
@@ -78,8 +82,8 @@ def wavefronts(addrs):
     return total
 
 
-def cost(n, thr, g, pe, te):
-    r, tl, lines = launch(n, thr)
+def cost(n, thr, g, pe, te, rp=0):
+    r, tl, lines = launch(n, thr, rp=rp)
     threads = tl * lines
     padn, trow = n + n // g + pe, lines + te
 
@@ -122,13 +126,13 @@ def cost(n, thr, g, pe, te):
     return total
 
 
-def best(n, thr):
-    default = cost(n, thr, 16, 1, 1)
+def best(n, thr, rp=0):
+    default = cost(n, thr, 16, 1, 1, rp)
     cands = []
     for g in (8, 16, 32):
         for pe in range(0, 9):
             for te in (0, 1, 2, 4, 8, 16):
-                cands.append((cost(n, thr, g, pe, te), n + n // g + pe + launch(n, thr)[2] + te, g, pe, te))
+                cands.append((cost(n, thr, g, pe, te, rp), n + n // g + pe + launch(n, thr, rp=rp)[2] + te, g, pe, te))
     c = min(cands)
     return (c[2], c[3], c[4]) if c[0] < default else (16, 1, 1)
 
@@ -152,15 +156,19 @@ def main():
                 continue
             g, pe, te = best(n, thr)
             if (g, pe, te) != (16, 1, 1):
-                rows.append((n, thr, g, pe, te))
+                rows.append((n, thr, 0, g, pe, te))
+    for n in TUNED:  # the alternative radix plans (default CTA shape)
+        g, pe, te = best(n, 0, 1)
+        if (g, pe, te) != (16, 1, 1):
+            rows.append((n, 0, 1, g, pe, te))
     out = sys.stdout
     out.write("// smem_layout.h -- generated by gen_smem_layout.py; do not edit.\n")
     out.write("// Shared-memory padding of the complex64 pass kernels with the fewest bank\n")
     out.write("// conflicts (pad(i) = i + i/g, line stride N + N/g + pe, tile row LINES + te).\n")
     out.write("#pragma once\n\nnamespace mdfft {\n\nstruct SmemLayout {\n    int g, pe, te;\n};\n\n")
-    out.write("__host__ __device__ constexpr SmemLayout smem_layout_c64(int n, int thr) {\n")
-    for n, thr, g, pe, te in rows:
-        out.write(f"    if (n == {n} && thr == {thr}) return SmemLayout{{{g}, {pe}, {te}}};\n")
+    out.write("__host__ __device__ constexpr SmemLayout smem_layout_c64(int n, int thr, int rp = 0) {\n")
+    for n, thr, rp, g, pe, te in rows:
+        out.write(f"    if (n == {n} && thr == {thr} && rp == {rp}) return SmemLayout{{{g}, {pe}, {te}}};\n")
     out.write("    return SmemLayout{16, 1, 1};\n}\n\n}  // namespace mdfft\n")
 
 

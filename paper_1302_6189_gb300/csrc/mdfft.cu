@@ -161,7 +161,19 @@ int64_t shrink_to_wave(Pass &ps, size_t elem, bool line_store) {
     return wave;
 }
 
-mdfft_status build_pass(mdfft_plan_s *p, int s) {
+// Launch arguments of pass s with the tile order `mapping` (kernel ps.k kept
+// if set, else the default kernel of the length):
+//  0  tiles of Bg lines consecutive along g, the output layout's fastest axis
+//     (other than f), and Bh along h, its next axis; the rest of the axes
+//     follow the output layout -- the store writes runs of Bg elements;
+//  1  input-chunk order: g and h are the input layout's second and third
+//     fastest axes and the rest follow the input layout, so consecutive
+//     tiles are consecutive lines of layout s and a tile of whole f_MD chunks
+//     (1-D and 2-D regimes) is exactly one chunk (CTA t owns chunk t); the
+//     store then writes elements Bg apart by g's output stride.
+// A pass that keeps f fastest in its output (lines stored whole) has only
+// tile order 0.
+mdfft_status layout_pass(const mdfft_plan_s *p, int s, int mapping, Pass &ps, bool keep_kernel = false) {
     const int M = p->M;
     const pl::Layout &L = p->order[s];
     pl::Layout nat;
@@ -169,20 +181,24 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     for (int i = 0; i < M; ++i) nat.axis[i] = i;
     // the last pass stores natural order, or layout L_M itself (MDFFT_PLAN_OUT_LAST_LAYOUT)
     const pl::Layout &Lo = (s + 1 < M) ? p->order[s + 1] : (p->flags & MDFFT_PLAN_OUT_LAST_LAYOUT) ? L : nat;
-    Pass &ps = p->pass[s];
     ps.f = L.axis[M - 1];
     ps.g = Lo.axis[M - 1];
     const bool line_store = ps.g == ps.f;  // output keeps f fastest: lines stored whole
     if (line_store && s + 1 < M) return fail(MDFFT_E_ORDER, "output layout keeps the transformed axis fastest");
+    if (line_store && mapping != 0) return fail(MDFFT_E_ARG, "a pass that stores whole lines has tile order 0 only");
+    if (mapping != 0 && mapping != 1) return fail(MDFFT_E_ARG, "tile order must be 0 or 1");
     if (line_store) ps.g = Lo.axis[M - 2];  // tile lines along the next axes of the layout
+    const pl::Layout &Lt = mapping == 1 ? L : Lo;  // the layout the tiles follow
+    if (mapping == 1) ps.g = M >= 2 ? L.axis[M - 2] : ps.f;
     ps.h = -1;
     for (int i = M - 2; i >= 0; --i)
-        if (Lo.axis[i] != ps.f && Lo.axis[i] != ps.g) {
-            ps.h = Lo.axis[i];
+        if (Lt.axis[i] != ps.f && Lt.axis[i] != ps.g) {
+            ps.h = Lt.axis[i];
             break;
         }
+    ps.mapping = mapping;
     ps.n = p->N[ps.f];
-    if (!lookup(p->dt, ps.n, &ps.k))
+    if (!keep_kernel && !lookup(p->dt, ps.n, &ps.k))
         return fail(MDFFT_E_UNSUPPORTED, "line length " + std::to_string(ps.n) + " is not built for this dtype");
 
     int64_t sin_[pl::kMaxDims], sout[pl::kMaxDims];
@@ -202,13 +218,13 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     a.out_sf = sout[ps.f];
     a.out_sg = sout[ps.g];
     a.line_store = line_store ? 1 : 0;
-    if ((line_store ? sout[ps.f] : sout[ps.g]) != 1 || sin_[ps.f] != 1)
+    if ((line_store ? sout[ps.f] : mapping == 0 ? sout[ps.g] : 1) != 1 || sin_[ps.f] != 1)
         return fail(MDFFT_E_ORDER, "internal: layout strides");
-    // remaining axes, fastest first in the output layout
+    // remaining axes, fastest first in the layout the tiles follow
     a.nrest = 0;
     ps.ctas = a.gblocks * a.hblocks;
     for (int i = M - 1; i >= 0; --i) {
-        int ax = Lo.axis[i];
+        int ax = Lt.axis[i];
         if (ax == ps.f || ax == ps.g || ax == ps.h) continue;
         a.rest_count[a.nrest] = p->N[ax];
         a.rest_in[a.nrest] = sin_[ax];
@@ -230,6 +246,32 @@ mdfft_status build_pass(mdfft_plan_s *p, int s) {
     a.scale = 1.0;
     a.scaled = 0;
     ps.grid = ps.k.persistent ? std::min<int64_t>(ps.ctas, wave) : ps.ctas;
+    return MDFFT_OK;
+}
+
+mdfft_status build_pass(mdfft_plan_s *p, int s) { return layout_pass(p, s, 0, p->pass[s]); }
+
+// Pass s run by kernel k with tile order m and tiles of Bg x Bh lines (the
+// autotuner's candidates and stored tunings); the count mode's owner maps
+// are those of the built pass.
+mdfft_status candidate_pass(const mdfft_plan_s *p, int s, const PassKernel &k, int m, int Bg, int Bh, Pass &out) {
+    Pass c = p->pass[s];
+    c.k = k;
+    mdfft_status st = layout_pass(p, s, m, c, true);
+    if (st != MDFFT_OK) return st;
+    PassArgs &a = c.args;
+    a.own_in = p->pass[s].args.own_in;
+    a.own_out = p->pass[s].args.own_out;
+    if (Bg < 1 || Bh < 1 || (int64_t)Bg * Bh > k.lines || Bg > a.Ng || Bh > a.Nh)
+        return fail(MDFFT_E_ARG, "tile shape does not fit the kernel or the pass");
+    a.Bg = Bg, a.Bh = Bh;
+    a.gblocks = (a.Ng + Bg - 1) / Bg;
+    a.hblocks = (a.Nh + Bh - 1) / Bh;
+    c.ctas = a.gblocks * a.hblocks;
+    for (int i = 0; i < a.nrest; ++i) c.ctas *= a.rest_count[i];
+    set_tile_divisors(a, c.ctas);
+    c.grid = k.persistent ? std::min<int64_t>(c.ctas, mdfft::detail::wave_ctas(k)) : c.ctas;
+    out = c;
     return MDFFT_OK;
 }
 
@@ -305,6 +347,21 @@ __global__ void twiddle_kernel(void *dst, int64_t n, mdfft::RadixPlan plan, int 
         off += ns * R;
         ns *= R;
     }
+}
+
+// Twiddle table of pass s for radix plan `plan` (the plan of the pass's
+// kernel), made on `st`.
+void make_twiddles(const mdfft_plan_s *p, int s, const mdfft::RadixPlan &plan, cudaStream_t st) {
+    const int entries = std::max(1, mdfft::tw_entries(plan));
+    twiddle_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, st>>>((char *)p->tw + p->pass[s].tw_offset,
+                                                                      p->pass[s].n, plan, p->dt == MDFFT_C128);
+}
+
+bool same_plan(const mdfft::RadixPlan &a, const mdfft::RadixPlan &b) {
+    if (a.S != b.S) return false;
+    for (int i = 0; i < a.S; ++i)
+        if (a.R[i] != b.R[i]) return false;
+    return true;
 }
 
 mdfft_status parse_order(int M, const int *order, std::vector<pl::Layout> &out) {
@@ -560,6 +617,7 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
     if (M < 2 || M > MDFFT_MAX_DIMS) return fail(MDFFT_E_UNSUPPORTED, "M must be in [2, 8]");
     constexpr unsigned kDecomp = MDFFT_PLAN_DECOMP_SLAB | MDFFT_PLAN_DECOMP_PENCIL | MDFFT_PLAN_DECOMP_VOLUMETRIC;
     if (flags & ~(MDFFT_PLAN_HOST_ONLY | MDFFT_PLAN_INPLACE | MDFFT_PLAN_PERSISTENT | MDFFT_PLAN_OUT_LAST_LAYOUT |
+                  MDFFT_PLAN_TUNE_RADIX |
                   kDecomp))
         return fail(MDFFT_E_ARG, "unknown flag");
     const unsigned decomp = flags & kDecomp;
@@ -643,11 +701,13 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
                     p->pass[s].grid = std::min<int64_t>(p->pass[s].ctas, mdfft::detail::wave_ctas(k));
                 }
             }
-        // twiddle tables: one per pass, 256-byte aligned inside one allocation
+        // twiddle tables: one per pass, 256-byte aligned inside one allocation,
+        // each with room for the table of any radix plan of its length (fewer
+        // than 2 n entries) so that autotuning can switch plans
         size_t off = 0;
         for (int s = 0; s < M; ++s) {
             p->pass[s].tw_offset = off;
-            const size_t entries = std::max(1, mdfft::tw_entries(p->pass[s].k.plan));
+            const size_t entries = std::max<size_t>(2 * (size_t)p->pass[s].n, mdfft::tw_entries(p->pass[s].k.plan));
             off += (entries * p->elem + 255) / 256 * 256;
         }
         p->tw_bytes = off;
@@ -669,12 +729,7 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
             }
             set_block_owners(p, tab);
         }
-        for (int s = 0; s < M; ++s) {
-            const int64_t n = p->pass[s].n;
-            const int entries = std::max(1, mdfft::tw_entries(p->pass[s].k.plan));
-            twiddle_kernel<<<(unsigned)((entries + 255) / 256), 256>>>((char *)p->tw + p->pass[s].tw_offset, n,
-                                                                       p->pass[s].k.plan, dt == MDFFT_C128);
-        }
+        for (int s = 0; s < M; ++s) make_twiddles(p, s, p->pass[s].k.plan, nullptr);
         const size_t bytes = (size_t)p->T * p->batch * p->elem;
         p->external_ws = !with_workspace;
         if (with_workspace && (e = cudaMalloc(&p->ws, bytes)) != cudaSuccess) {
@@ -919,6 +974,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && (uintptr_t)in % 16 == 0 &&
                     (uintptr_t)out % 16 == 0)
                     variants.push_back(k);
+            if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
         }
         if (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) {
             const int tc = p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16;
@@ -926,6 +982,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
         }
         float best_ms = -1.f, default_ms = -1.f;
         Pass best = ps;
+        mdfft::RadixPlan table = ps.k.plan;  // the plan the pass's twiddle table is made for
         for (size_t v = 0; v < variants.size() && result == MDFFT_OK; ++v) {
             const PassKernel &kv = variants[v];
             if (kv.smem > 48 * 1024 &&
@@ -933,55 +990,60 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 result = fail(MDFFT_E_CUDA, "cudaFuncSetAttribute");
                 break;
             }
-            // tile shapes: the default choice and powers of two along g
-            std::vector<std::pair<int, int>> tiles;
-            int bg0 = 1, bh0 = 1;
-            choose_tile(kv.lines, ps.args.Ng, ps.args.Nh, p->elem, &bg0, &bh0);
-            tiles.push_back({bg0, bh0});
-            for (int bg = kv.lines; bg >= 4; bg /= 2) {
-                if (bg > ps.args.Ng) continue;
-                const int bh = (int)std::min<int64_t>(ps.args.Nh, kv.lines / bg);
-                if (std::find(tiles.begin(), tiles.end(), std::make_pair(bg, bh)) == tiles.end())
-                    tiles.push_back({bg, bh});
+            if (!same_plan(kv.plan, table)) {  // timing with the twiddles of the variant's own radix plan
+                make_twiddles(p, s, kv.plan, st);
+                table = kv.plan;
             }
-            for (size_t ti = 0; ti < tiles.size(); ++ti) {
-                Pass cand = ps;
-                cand.k = kv;
-                PassArgs &a = cand.args;
-                a.Bg = tiles[ti].first, a.Bh = tiles[ti].second;
-                a.gblocks = (a.Ng + a.Bg - 1) / a.Bg;
-                a.hblocks = (a.Nh + a.Bh - 1) / a.Bh;
-                cand.ctas = a.gblocks * a.hblocks;
-                for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
-                set_tile_divisors(a, cand.ctas);
-                cand.grid = kv.persistent ? std::min<int64_t>(cand.ctas, mdfft::detail::wave_ctas(kv)) : cand.ctas;
-                a.in = in;
-                a.out = out;
-                a.tw = (const char *)p->tw + ps.tw_offset;
-                a.scale = 1.0;
-                a.scaled = 0;
-                a.ntiles = cand.ctas;
-                a.err = p->err;
-                void *args[] = {&a};
-                cudaError_t e = cudaSuccess;
-                for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.grid), dim3(kv.threads), args, kv.smem, st);
-                cudaEventRecord(e0, st);
-                for (int r = 0; r < reps && e == cudaSuccess; ++r)
-                    e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.grid), dim3(kv.threads), args, kv.smem, st);
-                cudaEventRecord(e1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) {
-                    result = cuda_fail(e, "autotune launch");
-                    break;
+            // tile orders: output-coalesced, and input-chunk order (not for
+            // the pipelined kernels, and not when the pass stores whole lines)
+            const int orders = (kv.persistent || ps.args.line_store) ? 1 : 2;
+            for (int m = 0; m < orders && result == MDFFT_OK; ++m) {
+                Pass base;
+                if (candidate_pass(p, s, kv, m, 1, 1, base) != MDFFT_OK) continue;
+                // tile shapes: the default choice and powers of two along g
+                std::vector<std::pair<int, int>> tiles;
+                int bg0 = 1, bh0 = 1;
+                choose_tile(kv.lines, base.args.Ng, base.args.Nh, p->elem, &bg0, &bh0);
+                tiles.push_back({bg0, bh0});
+                for (int bg = kv.lines; bg >= 4; bg /= 2) {
+                    if (bg > base.args.Ng) continue;
+                    const int bh = (int)std::min<int64_t>(base.args.Nh, kv.lines / bg);
+                    if (std::find(tiles.begin(), tiles.end(), std::make_pair(bg, bh)) == tiles.end())
+                        tiles.push_back({bg, bh});
                 }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= (float)reps;
-                if (v == 0 && ti == 0) default_ms = ms;
-                if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = cand;
+                for (size_t ti = 0; ti < tiles.size(); ++ti) {
+                    Pass cand;
+                    if (candidate_pass(p, s, kv, m, tiles[ti].first, tiles[ti].second, cand) != MDFFT_OK) continue;
+                    PassArgs a = cand.args;
+                    a.in = in;
+                    a.out = out;
+                    a.tw = (const char *)p->tw + ps.tw_offset;
+                    a.scale = 1.0;
+                    a.scaled = 0;
+                    a.ntiles = cand.ctas;
+                    a.err = p->err;
+                    void *args[] = {&a};
+                    cudaError_t e = cudaSuccess;
+                    for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+                        e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.grid), dim3(kv.threads), args, kv.smem, st);
+                    cudaEventRecord(e0, st);
+                    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                        e = cudaLaunchKernel(kv.fn, dim3((unsigned)cand.grid), dim3(kv.threads), args, kv.smem, st);
+                    cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess) {
+                        result = cuda_fail(e, "autotune launch");
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= (float)reps;
+                    if (v == 0 && m == 0 && ti == 0) default_ms = ms;
+                    if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = cand;
+                }
             }
         }
+        if (!same_plan(best.k.plan, table)) make_twiddles(p, s, best.k.plan, st);  // the chosen kernel's table
         if (result != MDFFT_OK) break;
         best.args.in = nullptr, best.args.out = nullptr, best.args.tw = nullptr, best.args.err = nullptr;
         ps = best;
@@ -997,11 +1059,14 @@ namespace {
 
 // The launch variants the autotuner chooses among, by code:
 // 0 default, 1 / 2 fixed 256 / 512-thread CTAs, 3 / 4 pipelined with 1 / 2 landing buffers,
-// 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 / 384-thread CTAs.
-constexpr int kTuningVariants = 8;
+// 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 / 384-thread CTAs,
+// 8 the alternative radix plan (default CTA shape rule).
+constexpr int kTuningVariants = 9;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     switch (variant) {
+        case 8:
+            return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_alt(n, k);
         case 6:
         case 7:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_thr(n, variant == 6 ? 192 : 384, k);
@@ -1036,7 +1101,7 @@ mdfft_status mdfft_plan_tuning(mdfft_plan_t p, int32_t *out, int cap) {
             if (tuning_kernel(p, s, v, &k) && k.fn == ps.k.fn) variant = v;
         }
         if (variant < 0) return fail(MDFFT_E_CUDA, "internal: unknown pass kernel");
-        out[4 * s] = variant, out[4 * s + 1] = ps.args.Bg, out[4 * s + 2] = ps.args.Bh, out[4 * s + 3] = 0;
+        out[4 * s] = variant, out[4 * s + 1] = ps.args.Bg, out[4 * s + 2] = ps.args.Bh, out[4 * s + 3] = ps.mapping;
     }
     return MDFFT_OK;
 }
@@ -1047,28 +1112,23 @@ mdfft_status mdfft_plan_set_tuning(mdfft_plan_t p, const int32_t *in, int n) {
     if (n != 4 * p->M) return fail(MDFFT_E_ARG, "expected 4 M entries");
     Pass next[MDFFT_MAX_DIMS];
     for (int s = 0; s < p->M; ++s) {  // validate everything before changing anything
-        Pass cand = p->pass[s];
         PassKernel k;
-        const int variant = in[4 * s], Bg = in[4 * s + 1], Bh = in[4 * s + 2];
+        const int variant = in[4 * s], Bg = in[4 * s + 1], Bh = in[4 * s + 2], mapping = in[4 * s + 3];
         if (!tuning_kernel(p, s, variant, &k)) return fail(MDFFT_E_ARG, "kernel variant not built for this pass");
         if ((variant == 3 || variant == 4) && k.lines != p->pass[s].k.lines)
             return fail(MDFFT_E_ARG, "pipelined variant needs the default tile lines");
-        PassArgs &a = cand.args;
-        if (Bg < 1 || Bh < 1 || (int64_t)Bg * Bh > k.lines || Bg > a.Ng || Bh > a.Nh)
-            return fail(MDFFT_E_ARG, "tile shape does not fit the kernel or the pass");
+        if (mapping != 0 && (k.persistent || mapping != 1))
+            return fail(MDFFT_E_ARG, "tile order must be 0, or 1 with a non-persistent kernel");
         if (k.smem > 48 * 1024 &&
             cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
             return fail(MDFFT_E_CUDA, "cudaFuncSetAttribute");
-        cand.k = k;
-        a.Bg = Bg, a.Bh = Bh;
-        a.gblocks = (a.Ng + Bg - 1) / Bg;
-        a.hblocks = (a.Nh + Bh - 1) / Bh;
-        cand.ctas = a.gblocks * a.hblocks;
-        for (int i = 0; i < a.nrest; ++i) cand.ctas *= a.rest_count[i];
-        cand.grid = k.persistent ? std::min<int64_t>(cand.ctas, mdfft::detail::wave_ctas(k)) : cand.ctas;
-        set_tile_divisors(a, cand.ctas);
-        next[s] = cand;
+        mdfft_status st = candidate_pass(p, s, k, mapping, Bg, Bh, next[s]);
+        if (st != MDFFT_OK) return st;
     }
+    for (int s = 0; s < p->M; ++s)
+        if (!same_plan(next[s].k.plan, p->pass[s].k.plan)) make_twiddles(p, s, next[s].k.plan, nullptr);
+    cudaError_t e = cudaDeviceSynchronize();  // the new tables ready for any stream
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle generation");
     for (int s = 0; s < p->M; ++s) p->pass[s] = next[s];
     drop_graphs(p);
     return MDFFT_OK;
@@ -1089,6 +1149,9 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {
     out->store_axis = ps.g;
     out->grid = ps.grid;
     out->persistent = ps.k.persistent;
+    out->stages = ps.k.plan.S;
+    for (int i = 0; i < 12; ++i) out->radix[i] = i < ps.k.plan.S ? ps.k.plan.R[i] : 0;
+    out->tile_order = ps.mapping;
     return MDFFT_OK;
 }
 

@@ -21,7 +21,8 @@ struct Pass {
     PassArgs args{};           // everything but in/out/tw/conj/scale/count pointers
     int64_t ctas = 0;          // tiles
     int64_t grid = 0;          // CTAs launched (= ctas, or one wave for persistent kernels)
-    size_t tw_offset = 0;      // byte offset of this pass's twiddle table
+    size_t tw_offset = 0;      // byte offset of this pass's twiddle table (room for 2 n entries: any radix plan)
+    int mapping = 0;           // tile order: 0 output-coalesced, 1 input-chunk order (see layout_pass)
 };
 
 // CTAs of one wave of kernel k on the current device (at least 1).

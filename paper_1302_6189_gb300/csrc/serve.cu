@@ -239,6 +239,7 @@ struct mdfft_server_s {
     int64_t next_id = 1;
     int depth = 2;  // steps in flight on the GPU at most; arrivals in between join the next step
     int chunk = 4;  // at most this many consecutive tiles dealt to a CTA at a time
+    int direct = 4;  // low load: at most this many requests with passes left run them as plain launches
     Slot slots[kSlots];
     int next_slot = 0;
     cudaEvent_t t0 = nullptr;
@@ -456,6 +457,33 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
         resolve_slot(s, sl);
     }
+    cudaError_t e = cudaSuccess;
+    if ((int)todo.size() <= s->direct && s->queue.empty()) {
+        // low load: every remaining pass of these requests, oldest first, as
+        // plain pass launches (stream order keeps each request's passes in order)
+        for (Request *r : todo) {
+            for (int pass = r->next_pass; pass < r->plan->M; ++pass) {
+                const mdfft::detail::Pass &ps = r->plan->pass[pass];
+                PassArgs a = pass_args(s, r, pass);
+                a.ntiles = ps.ctas;
+                void *args[] = {&a};
+                e = cudaLaunchKernel(ps.k.fn, dim3((unsigned)ps.grid), dim3(ps.k.threads), args, ps.k.smem, s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+                s->stats.kernel_launches++;
+            }
+            r->next_pass = r->plan->M;
+            r->last_slot = r->slot = s->next_slot;
+            sl.finishing.push_back(r);
+            s->stats.direct_requests++;
+        }
+        e = cudaEventRecord(sl.done, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        sl.busy = true;
+        s->next_slot = (s->next_slot + 1) % kSlots;
+        s->stats.steps++;
+        if (launched) *launched = 1;
+        return MDFFT_OK;
+    }
     Table *tab = sl.host;
     int n = 0;
     int64_t total = 0;
@@ -487,7 +515,6 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     // the step's tiles spread over every CTA first: chunks of total / grid tiles, at most s->chunk
     tab->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(s->chunk, total / std::max(1, s->grid)));
     tab->total = total;
-    cudaError_t e = cudaSuccess;
     if (n > 0) {
         if (sl.copy) {  // copy only the header and the items of this step
             const size_t used = offsetof(Table, items) + (size_t)n * sizeof(Item);
@@ -629,6 +656,12 @@ mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas) {
 mdfft_status mdfft_server_set_chunk(mdfft_server_t s, int chunk) {
     if (!s || chunk < 1 || chunk > 64) return fail(MDFFT_E_ARG, "chunk must be in [1, 64]");
     s->chunk = chunk;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_server_set_direct(mdfft_server_t s, int max_requests) {
+    if (!s || max_requests < 0 || max_requests > 64) return fail(MDFFT_E_ARG, "direct threshold must be in [0, 64]");
+    s->direct = max_requests;
     return MDFFT_OK;
 }
 

@@ -25,6 +25,7 @@ MDFFT_C64, MDFFT_C128, MDFFT_C64_TC_FP16, MDFFT_C64_TC_BF16 = 0, 1, 2, 3
 MDFFT_PLAN_HOST_ONLY, MDFFT_PLAN_INPLACE, MDFFT_PLAN_PERSISTENT = 0x1, 0x2, 0x4
 MDFFT_PLAN_DECOMP_SLAB, MDFFT_PLAN_DECOMP_PENCIL, MDFFT_PLAN_DECOMP_VOLUMETRIC = 0x10, 0x20, 0x40
 MDFFT_PLAN_OUT_NATURAL, MDFFT_PLAN_OUT_LAST_LAYOUT = 0x0, 0x80
+MDFFT_PLAN_TUNE_RADIX = 0x100
 DECOMPOSITIONS = {"rowwise": 0, "slab": MDFFT_PLAN_DECOMP_SLAB, "pencil": MDFFT_PLAN_DECOMP_PENCIL,
                   "volumetric": MDFFT_PLAN_DECOMP_VOLUMETRIC}
 DTYPES = {"c64": MDFFT_C64, "c128": MDFFT_C128, "c64_tc_fp16": MDFFT_C64_TC_FP16,
@@ -46,14 +47,15 @@ class MdfftComm(ctypes.Structure):
 class MdfftPassInfo(ctypes.Structure):
     _fields_ = [("line_length", i64), ("tile_g", c_int), ("tile_h", c_int), ("threads", c_int),
                 ("smem_bytes", c_int), ("ctas", i64), ("fft_axis", c_int), ("store_axis", c_int),
-                ("grid", i64), ("persistent", c_int)]
+                ("grid", i64), ("persistent", c_int), ("stages", c_int), ("radix", c_int * 12),
+                ("tile_order", c_int)]
 
 
 class MdfftServerStats(ctypes.Structure):
     _fields_ = [("submitted", i64), ("admitted", i64), ("completed", i64), ("steps", i64),
                 ("graph_launches", i64), ("kernel_launches", i64), ("inflight", i64), ("queued", i64),
                 ("bytes_in_use", c_size_t), ("budget_bytes", c_size_t), ("grid_ctas", c_int),
-                ("cancelled", i64)]
+                ("cancelled", i64), ("direct_requests", i64)]
 
 
 SIGNATURES = {
@@ -99,6 +101,7 @@ SIGNATURES = {
     "mdfft_server_set_grid": (c_int, [c_void_p, c_int]),
     "mdfft_server_set_depth": (c_int, [c_void_p, c_int]),
     "mdfft_server_set_chunk": (c_int, [c_void_p, c_int]),
+    "mdfft_server_set_direct": (c_int, [c_void_p, c_int]),
     "mdfft_server_get_stats": (c_int, [c_void_p, P_(MdfftServerStats)]),
     "mdfft_server_destroy": (c_int, [c_void_p]),
 }
@@ -189,21 +192,21 @@ def mdfft_selftest_wait(arrive, limit_us):
     return st, waited.value
 
 
-TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384")
+TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384", "radix_alt")
 
 
 def mdfft_plan_tuning(plan, M):
-    """[{"variant": ..., "tile_g": ..., "tile_h": ...} per pass] (JSON-friendly)."""
+    """[{"variant": ..., "tile_g": ..., "tile_h": ..., "tile_order": ...} per pass] (JSON-friendly)."""
     arr = (ctypes.c_int32 * (4 * M))()
     _check(_lib.mdfft_plan_tuning(plan, arr, 4 * M), "mdfft_plan_tuning")
-    return [{"variant": TUNING_VARIANTS[arr[4 * s]], "tile_g": arr[4 * s + 1], "tile_h": arr[4 * s + 2]}
-            for s in range(M)]
+    return [{"variant": TUNING_VARIANTS[arr[4 * s]], "tile_g": arr[4 * s + 1], "tile_h": arr[4 * s + 2],
+             "tile_order": arr[4 * s + 3]} for s in range(M)]
 
 
 def mdfft_plan_set_tuning(plan, tuning):
     vals = []
     for t in tuning:
-        vals += [TUNING_VARIANTS.index(t["variant"]), int(t["tile_g"]), int(t["tile_h"]), 0]
+        vals += [TUNING_VARIANTS.index(t["variant"]), int(t["tile_g"]), int(t["tile_h"]), int(t.get("tile_order", 0))]
     arr = (ctypes.c_int32 * len(vals))(*vals)
     _check(_lib.mdfft_plan_set_tuning(plan, arr, len(vals)), "mdfft_plan_set_tuning")
 
@@ -287,7 +290,9 @@ def mdfft_exec_host(plan, in_host_ptr, out_host_ptr, dev_in_ptr, dev_out_ptr, di
 def mdfft_pass_describe(plan, s):
     info = MdfftPassInfo()
     _check(_lib.mdfft_pass_describe(plan, int(s), ctypes.byref(info)), "mdfft_pass_describe")
-    return {f: getattr(info, f) for f, _ in MdfftPassInfo._fields_}
+    d = {f: getattr(info, f) for f, _ in MdfftPassInfo._fields_ if f != "radix"}
+    d["radix"] = [info.radix[i] for i in range(info.stages)]
+    return d
 
 
 def mdfft_plan_autotune(plan, in_ptr, out_ptr, reps, stream, M):
@@ -406,6 +411,10 @@ def mdfft_server_set_chunk(server, chunk):
 
 def mdfft_server_set_depth(server, depth):
     _check(_lib.mdfft_server_set_depth(server, int(depth)), "mdfft_server_set_depth")
+
+
+def mdfft_server_set_direct(server, max_requests):
+    _check(_lib.mdfft_server_set_direct(server, int(max_requests)), "mdfft_server_set_direct")
 
 
 def mdfft_server_get_stats(server):
@@ -617,6 +626,9 @@ class Server:
 
     def set_depth(self, depth):
         mdfft_server_set_depth(self.handle, depth)
+
+    def set_direct(self, max_requests):
+        mdfft_server_set_direct(self.handle, max_requests)
 
     def stats(self):
         return mdfft_server_get_stats(self.handle)

@@ -201,3 +201,30 @@ def test_serving_bench_lengths_mix_equals_alone_and_oracle():
             ref = ref / ref.size
         y = outs[k].cpu().numpy().astype(np.complex128)
         assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= 1e-5, shapes[k]
+
+
+@pytest.mark.parametrize("direct", [0, 2, 64])
+def test_low_load_direct_launches_give_the_same_bits(direct):
+    # requests submitted one at a time with the server stepped in between: at
+    # low load (nothing queued, at most `direct` requests with passes left)
+    # their passes run as plain launches; every result equals mdfft_exec's
+    shapes = [(48, 64, 96), (32, 32, 32, 32), (192, 48, 64), (64, 64, 64), (20, 30, 40)]
+    xs = [torch.from_numpy(si.uniform_complex(sh, 1800 + i, np.complex64)).to(DEV) for i, sh in enumerate(shapes)]
+    outs = [torch.empty_like(x) for x in xs]
+    with md.Server(budget_bytes=1 << 30, max_inflight=8) as srv:
+        srv.set_direct(direct)
+        ids = []
+        for x, y in zip(xs, outs):
+            ids.append(srv.submit(x, y))
+            srv.step()
+        srv.drain()
+        st = srv.stats()
+        assert st["completed"] == len(shapes)
+        if direct == 0:
+            assert st["direct_requests"] == 0
+        else:
+            assert st["direct_requests"] >= 1
+        with pytest.raises(md.MdfftError):
+            srv.set_direct(-1)
+    for sh, x, y in zip(shapes, xs, outs):
+        assert torch.equal(y, alone(sh, x, -1, False)), sh

@@ -42,12 +42,14 @@ def test_idle_lanes_and_broadcast():
 def _committed():
     rows = {}
     with open(os.path.join(CSRC, "smem_layout.h")) as f:
-        for m in re.finditer(r"n == (\d+) && thr == (\d+)\) return SmemLayout\{(\d+), (\d+), (\d+)\}", f.read()):
-            n, thr, g, pe, te = map(int, m.groups())
-            rows[(n, thr)] = (g, pe, te)
+        for m in re.finditer(r"n == (\d+) && thr == (\d+) && rp == (\d+)\) return SmemLayout\{(\d+), (\d+), (\d+)\}",
+                             f.read()):
+            n, thr, rp, g, pe, te = map(int, m.groups())
+            rows[(n, thr, rp)] = (g, pe, te)
     return rows
 
 
-@pytest.mark.parametrize("n,thr", [(48, 256), (128, 256), (64, 0), (256, 0)])
-def test_committed_table_matches_the_generator(n, thr):
-    assert _committed().get((n, thr), (16, 1, 1)) == gen.best(n, thr)
+@pytest.mark.parametrize("n,thr,rp", [(48, 256, 0), (128, 256, 0), (64, 0, 0), (256, 0, 0), (24, 192, 0),
+                                      (64, 0, 1)])
+def test_committed_table_matches_the_generator(n, thr, rp):
+    assert _committed().get((n, thr, rp), (16, 1, 1)) == gen.best(n, thr, rp)
