@@ -116,9 +116,9 @@ typedef enum {
  *          for) unless MDFFT_PLAN_HOST_ONLY is set (then any dim >= 1).
  *   P      number of virtual processes, 1 <= P <= N_1 ... N_M (f_MD, Sec. 3.2).
  *   order  M*M axis ids as described above, or NULL for the order with the
- *          smallest total communication amount (mdfft_order_search, M <= 5)
- *          or the balanced-split heuristic's order (mdfft_order_heuristic,
- *          M >= 6).
+ *          smallest total communication amount (mdfft_order_search: M <= 5,
+ *          and M = 6 where that search is affordable) or else the
+ *          balanced-split heuristic's order (mdfft_order_heuristic).
  *   dt     an mdfft_dtype.
  *   flags  MDFFT_PLAN_* bits.
  * Twiddles are made on the device in FP64 (sincospi) and rounded to the
@@ -256,10 +256,15 @@ mdfft_status mdfft_plan_order(mdfft_plan_t plan, int *order_out);
 /*
  * mdfft_order_search -- the order with the smallest (want_worst = 0) or
  * largest (want_worst = 1) total amount over all (M-1)!^M orders (Sec. 3.2,
- * Table 1), by dynamic programming over (step, layout, transformed axes)
- * with the pairwise amounts from box intersection.  Ties go to the
- * lexicographically smallest sequence of layouts.  order_out: M*M ints;
- * total: the amount.  M <= 6 (E_UNSUPPORTED above).
+ * Table 1), by dynamic programming over (step, layout, transformed axes).
+ * Layouts that cut the same leading axes in the same order (their regime's
+ * first k axes) own every point alike, so one pairwise amount serves each
+ * pair of such classes: counted over owner arrays on grids of up to 2^16
+ * points, by box intersection above.  Ties go to the lexicographically
+ * smallest sequence of layouts.  order_out: M*M ints; total: the amount.
+ * M <= 6 (E_UNSUPPORTED above); E_UNSUPPORTED too when the amounts would
+ * cost more than about 4e10 operations (large 6-D grids at high P: use
+ * mdfft_order_heuristic).
  */
 mdfft_status mdfft_order_search(int M, const int64_t N[], int64_t P, int want_worst, int *order_out,
                                 int64_t *total);

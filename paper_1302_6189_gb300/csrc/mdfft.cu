@@ -660,8 +660,10 @@ mdfft_status mdfft::detail::plan_create(mdfft_plan_t *out, int M, const int64_t 
     } else {
         int64_t total;
         std::string err;
-        const bool ok = M <= 5 ? pl::search_order(M, p->N, P, false, p->order, total, err)
-                               : pl::heuristic_order(M, p->N, P, p->order, total, err);
+        // the exact search up to 6 dims (6: when affordable), else the balanced-split heuristic
+        bool ok = M <= 6 && pl::search_order(M, p->N, P, false, p->order, total, err);
+        if (!ok && M == 6 && err.rfind("the exact order search is too large", 0) == 0) err.clear();
+        if (!ok && err.empty()) ok = pl::heuristic_order(M, p->N, P, p->order, total, err);
         if (!ok) {
             release(p);
             return fail(MDFFT_E_UNSUPPORTED, "order search: " + err);
@@ -874,7 +876,8 @@ mdfft_status mdfft_order_search(int M, const int64_t N[], int64_t P, int want_wo
     if (P < 1 || P > T) return fail(MDFFT_E_RANGE, "P must be in [1, N_1 ... N_M]");
     std::vector<pl::Layout> order;
     std::string err;
-    if (!pl::search_order(M, N, P, want_worst != 0, order, *total, err)) return fail(MDFFT_E_ARG, err);
+    if (!pl::search_order(M, N, P, want_worst != 0, order, *total, err))
+        return fail(err.rfind("the exact order search is too large", 0) == 0 ? MDFFT_E_UNSUPPORTED : MDFFT_E_ARG, err);
     for (int s = 0; s < M; ++s)
         for (int i = 0; i < M; ++i) order_out[s * M + i] = order[s].axis[i];
     return MDFFT_OK;

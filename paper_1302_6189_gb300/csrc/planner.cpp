@@ -6,7 +6,8 @@
 // text on Fig. 2) and the order count of the C_MD equation.  Amounts are
 // computed by intersecting the boxes that make up each chunk, and the order
 // search is a dynamic programme over (step, layout, axes already
-// transformed): neither enumerates points or orders.
+// transformed) that does not enumerate orders (on grids of up to 2^16 points
+// it compares owner arrays, one per ownership class of layouts).
 #include "planner.h"
 
 #include <algorithm>
@@ -182,19 +183,64 @@ std::string check_order(int M, const std::vector<Layout> &order) {
 
 namespace {
 
+// The owner of a point in layout L depends only on the coordinates of L's
+// first k axes (k = L's regime, Sec. 3.2): layouts with the same first k
+// axes, in the same order, have the same ownership.  The search computes one
+// amount per pair of such keys.  On small grids an amount is a count over
+// the owner arrays of the two keys (T points), else box intersection.
 struct SearchCtx {
     int M;
     const int64_t *N;
-    int64_t P;
+    int64_t P, T;
     bool worst;
     std::vector<Layout> perms;
-    std::vector<int64_t> pair;     // lazily filled pairwise amounts, -1 = unknown
+    std::vector<int> key;                     // key id of every layout
+    std::vector<int> key_rep;                 // a layout of every key
+    std::vector<std::vector<int32_t>> owners; // owner array (natural index order) per key, on demand
+    std::vector<int64_t> pair;     // lazily filled amounts per key pair, -1 = unknown
     std::vector<int64_t> memo;     // [layer][perm][mask], INT64_MIN = unknown
-    int F, masks;
+    int F, K, masks;
+    static constexpr int64_t kOwnerArrayPoints = 1 << 16;
+
+    const std::vector<int32_t> &owner_array(int k) {
+        std::vector<int32_t> &o = owners[k];
+        if (o.empty()) {
+            const Layout &L = perms[key_rep[k]];
+            int64_t st[kMaxDims], s = 1;  // stride in L of every natural axis
+            for (int i = M - 1; i >= 0; --i) st[L.axis[i]] = s, s *= N[L.axis[i]];
+            int64_t d[kMaxDims];
+            layout_dims(L, N, d);
+            const int kr = regime(M, d, P);
+            int64_t lead = 1, tail = 1;
+            for (int i = 0; i < M; ++i) (i < kr ? lead : tail) *= d[i];
+            o.resize((size_t)T);
+            int64_t c[kMaxDims];
+            for (int64_t x = 0; x < T; ++x) {  // owner_of() of the point, its q = y / tail
+                digits(M, N, x, c);
+                int64_t y = 0;
+                for (int i = 0; i < M; ++i) y += c[i] * st[i];
+                o[(size_t)x] = (int32_t)(((y / tail + 1) * P - 1) / lead);
+            }
+        }
+        return o;
+    }
 
     int64_t amount(int f, int g) {
-        int64_t &v = pair[(size_t)f * F + g];
-        if (v < 0) v = transition_amount(M, N, P, perms[f], perms[g]);
+        const int a = key[f], b = key[g];
+        int64_t &v = pair[(size_t)a * K + b];
+        if (v < 0) {
+            if (a == b) {
+                v = 0;
+            } else if (T <= kOwnerArrayPoints) {
+                const std::vector<int32_t> &oa = owner_array(a);
+                const std::vector<int32_t> &ob = owner_array(b);
+                int64_t moved = 0;
+                for (int64_t x = 0; x < T; ++x) moved += oa[(size_t)x] != ob[(size_t)x];
+                v = moved;
+            } else {
+                v = transition_amount(M, N, P, perms[f], perms[g]);
+            }
+        }
         return v;
     }
     bool better(int64_t a, int64_t b) const { return worst ? a > b : a < b; }
@@ -240,18 +286,33 @@ bool search_order(int M, const int64_t *N, int64_t P, bool want_worst, std::vect
         return false;
     }
     SearchCtx c;
-    c.M = M, c.N = N, c.P = P, c.worst = want_worst;
+    c.M = M, c.N = N, c.P = P, c.T = T, c.worst = want_worst;
     int ids[kMaxDims];
     for (int i = 0; i < M; ++i) ids[i] = i;
+    std::vector<std::vector<int>> keys;
     do {  // lexicographic permutations; index 0 is the natural layout
         Layout L;
         L.M = M;
         std::memcpy(L.axis, ids, sizeof(int) * M);
+        int64_t d[kMaxDims];
+        layout_dims(L, N, d);
+        std::vector<int> k(ids, ids + regime(M, d, P));
+        const size_t id = std::find(keys.begin(), keys.end(), k) - keys.begin();
+        if (id == keys.size()) keys.push_back(k), c.key_rep.push_back((int)c.perms.size());
+        c.key.push_back((int)id);
         c.perms.push_back(L);
     } while (std::next_permutation(ids, ids + M));
     c.F = (int)c.perms.size();
+    c.K = (int)keys.size();
     c.masks = 1 << M;
-    c.pair.assign((size_t)c.F * c.F, -1);
+    // the exact search must stay affordable: amounts of every key pair
+    const double per_pair = T <= SearchCtx::kOwnerArrayPoints ? (double)T : (double)P * 4.0 * M * M;
+    if ((double)c.K * c.K * per_pair > 4e10) {
+        err = "the exact order search is too large for this grid and P (use the heuristic)";
+        return false;
+    }
+    c.owners.resize(c.K);
+    c.pair.assign((size_t)c.K * c.K, -1);
     c.memo.assign((size_t)M * c.F * c.masks, INT64_MIN);
 
     unsigned mask = 1u << (M - 1);

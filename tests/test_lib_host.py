@@ -181,13 +181,53 @@ def test_heuristic_for_six_to_eight_dims():
             order, total = md.mdfft_order_heuristic(N, P)
             assert total * P == T * (P - 1)
             assert oracle.comm_volume(N, P, order)["total"] == total
-    # without an order, plans of 6-8 dims use it
-    for N in [(4, 2, 3, 2, 4, 2), (2, 2, 3, 2, 2, 2, 2), (2,) * 8]:
+    # without an order, plans of 7-8 dims use it (6 dims: the exact search below)
+    for N in [(2, 2, 3, 2, 2, 2, 2), (2,) * 8]:
         h = md.mdfft_plan(N, 4, None, "c64", HOST)
         try:
             assert md.mdfft_plan_order(h, len(N)) == md.mdfft_order_heuristic(N, 4)[0]
         finally:
             md.mdfft_destroy(h)
+
+
+@pytest.mark.parametrize("N,P,ratio", [((4,) * 6, 4, 1.0), ((4,) * 6, 64, 1.0), ((4,) * 6, 256, 1.325),
+                                       ((4,) * 6, 1024, 1.0625), ((2, 3, 4, 2, 3, 4), 50, 1352 / 1187),
+                                       ((6, 4, 5, 3, 4, 2), 100, 1.0), ((8,) * 6, 64, 1.0)])
+def test_exact_six_dim_search_against_the_heuristic(N, P, ratio):
+    # 6 dims: 120^6 = 3e12 orders (Table 1) rule out enumeration, but the
+    # dynamic programme over (step, layout, transformed axes) finds the
+    # optimum.  Its order's amount is recounted point by point by the oracle
+    # (owner arrays, brute force), it is never above the heuristic's, it
+    # reaches the closed form T (1 - 1/P) in a cube's low regime, and above
+    # the low regimes it shows the heuristic is not optimal (ratio recorded)
+    order, total = md.mdfft_order_search(N, P, 0)
+    assert oracle.comm_volume(N, P, order)["total"] == total
+    horder, htotal = md.mdfft_order_heuristic(N, P)
+    assert htotal >= total
+    assert htotal == pytest.approx(ratio * total, rel=1e-9)
+    M, T = len(N), int(np.prod(N))
+    assert order[0] == list(range(M)) and sorted(L[-1] for L in order) == list(range(M))
+    if len(set(N)) == 1 and N[0] ** (M // 2) % P == 0:
+        assert total * P == T * (P - 1)
+    worst_order, worst = md.mdfft_order_search(N, P, 1)
+    assert oracle.comm_volume(N, P, worst_order)["total"] == worst >= htotal
+    # a 6-D plan without an order takes the exact search's order
+    h = md.mdfft_plan(N, P, None, "c64", HOST)
+    try:
+        assert md.mdfft_plan_order(h, M) == order
+    finally:
+        md.mdfft_destroy(h)
+
+
+def test_exact_six_dim_search_refuses_what_it_cannot_afford():
+    with pytest.raises(md.MdfftError) as e:
+        md.mdfft_order_search((8,) * 6, 4096, 0)
+    assert e.value.status == -7  # E_UNSUPPORTED: the heuristic is the way there
+    h = md.mdfft_plan((8,) * 6, 4096, None, "c64", HOST)  # plans fall back to the heuristic
+    try:
+        assert md.mdfft_plan_order(h, 6) == md.mdfft_order_heuristic((8,) * 6, 4096)[0]
+    finally:
+        md.mdfft_destroy(h)
 
 
 # ----------------------------------------------------------------------------- comparison methods (Sec. 4)
