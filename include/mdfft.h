@@ -528,6 +528,53 @@ mdfft_status mdfft_server_destroy(mdfft_server_t s);
 mdfft_status mdfft_exec_noalloc(int M, const int64_t N[], const int *order, mdfft_dtype dt, const void *in_dev,
                                 void *out_dev, int dir, int normalize, mdfft_stream_t stream);
 
+/*
+ * Distributed data plane (Sec. 1's setting; the "Transpose" steps of Fig. 4)
+ * for the P virtual processes placed on G devices: device g holds processes
+ * floor(gP/G) .. floor((g+1)P/G) - 1, i.e. one contiguous row-major range of
+ * every layout.  A transform on G devices runs, for step s = 0 .. M-1 on
+ * every device g:
+ *   mdfft_dist_lines(s)   the 1-D DFTs along layout s's last axis over the
+ *                         device's range (lines whole, no transpose);
+ *   mdfft_dist_pack(s)    the range's points grouped by destination device
+ *                         h = 0 .. G-1 (its owner in layout s+1, natural
+ *                         order after the last step) into a send buffer;
+ *   the caller's all-to-all-v: device g sends counts[g*G + h] points to h
+ *                         (mdfft_exchange_counts(plan, s, G, counts)), h's
+ *                         receive buffer holds the groups from g = 0 .. G-1
+ *                         back to back;
+ *   mdfft_dist_unpack(s)  the receive buffer into the device's range of
+ *                         layout s+1.
+ * Group (g -> h) lists its points in an order both sides derive from the plan
+ * (the intersections of the planner's boxes of the two ranges, each in layout
+ * s+1's row-major order), so only values travel.  The library moves no data
+ * between devices and needs no peer access: remote data reaches local memory
+ * through the caller's transport (NCCL's grouped send/recv through
+ * torch.distributed, or host copies) before the unpack.  Plans must be
+ * row-wise (no MDFFT_PLAN_DECOMP_*), of batch 1, with natural output order.
+ * Local arrays are device memory of the range's length (x1 - x0 of
+ * mdfft_dist_local_range); a send or receive buffer holds sum of the row or
+ * column of counts.  The first pack or unpack of a (step, G, device)
+ * allocates its copy list on the device (kept by the plan).  Everything is
+ * asynchronous on `stream`.  Errors: E_ARG; E_UNSUPPORTED from
+ * mdfft_dist_lines when a device boundary splits a line of that step (the
+ * M-D regime with too many devices).
+ */
+/* [*x0, *x1): device g's range of layout `step` (0 .. M; M: natural order). */
+mdfft_status mdfft_dist_local_range(mdfft_plan_t plan, int step, int G, int g, int64_t *x0, int64_t *x1);
+/* Step `step`'s line DFTs of device g (dir, normalize as for mdfft_exec: the
+ * inverse conjugates step 0's input and step M-1's output, normalize scales
+ * step M-1's output by 1/T); in_local == out_local is allowed. */
+mdfft_status mdfft_dist_lines(mdfft_plan_t plan, int step, int G, int g, const void *in_local, void *out_local,
+                              int dir, int normalize, mdfft_stream_t stream);
+/* Device g's range of layout `step` -> send buffer, grouped by destination. */
+mdfft_status mdfft_dist_pack(mdfft_plan_t plan, int step, int G, int g, const void *local, void *sendbuf,
+                             mdfft_stream_t stream);
+/* Receive buffer (groups from every source device, in device order) ->
+ * device h's range of layout step+1. */
+mdfft_status mdfft_dist_unpack(mdfft_plan_t plan, int step, int G, int h, const void *recvbuf, void *local,
+                               mdfft_stream_t stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *mdfft_last_error(void);
 

@@ -9,4 +9,5 @@ from .mdfft import (  # noqa: F401
     MDFFT_PLAN_DECOMP_VOLUMETRIC, DECOMPOSITIONS, LIB_PATH, MdfftError, Plan, Server, format_order, mdfft_chunk, mdfft_comm_volume,
     mdfft_destroy, mdfft_exec, mdfft_exec_counted, mdfft_exec_graph, mdfft_selftest_wait, mdfft_exec_host, mdfft_exec_noalloc, mdfft_exchange_counts, mdfft_block_grid, mdfft_last_error, mdfft_launches_per_exec,
     mdfft_order_heuristic, mdfft_order_search, mdfft_pass_describe, mdfft_pass_times, mdfft_pass_timing, mdfft_plan, mdfft_plan_batched, mdfft_plan_tuning, mdfft_plan_set_tuning,
-    mdfft_plan_order, mdfft_supported_length, mdfft_workspace_size, mdfft_fp64_rate_probe, parse_order)
+    mdfft_plan_order, mdfft_supported_length, mdfft_workspace_size, mdfft_fp64_rate_probe, parse_order,
+    DistPlan, torch_exchange, mdfft_dist_local_range, mdfft_dist_lines, mdfft_dist_pack, mdfft_dist_unpack)

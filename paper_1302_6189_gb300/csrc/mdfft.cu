@@ -391,6 +391,8 @@ void release(mdfft_plan_s *p) {
     for (auto &g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (p->capture) cudaStreamDestroy(p->capture);
+    for (auto &b : p->dist_boxes)
+        if (b.dev) cudaFree(b.dev);
     delete p;
 }
 

@@ -86,4 +86,12 @@ struct mdfft_plan_s {
     std::vector<GraphEntry> graphs;
     uint64_t graph_tick = 0;
     cudaStream_t capture = nullptr;  // private stream the passes are captured on
+    // distributed data plane: copy boxes per (step, G, device, pack) in device memory, made on first use
+    struct DistBoxes {
+        std::vector<int64_t> key;
+        void *dev = nullptr;
+        int n = 0;
+        int64_t total = 0;
+    };
+    std::vector<DistBoxes> dist_boxes;
 };

@@ -85,6 +85,10 @@ SIGNATURES = {
     "mdfft_pattern_probe": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, P_(ctypes.c_float)]),
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_fp64_rate_probe": (c_int, [c_void_p, c_int, i64, c_void_p, P_(ctypes.c_double)]),
+    "mdfft_dist_local_range": (c_int, [c_void_p, c_int, c_int, c_int, P_(i64), P_(i64)]),
+    "mdfft_dist_lines": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "mdfft_dist_pack": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "mdfft_dist_unpack": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "mdfft_supported_length": (c_int, [i64, c_int]),
     "mdfft_destroy": (c_int, [c_void_p]),
     "mdfft_exec_noalloc": (c_int, [c_int, P_(i64), P_(c_int), c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -315,6 +319,28 @@ def mdfft_fp64_rate_probe(out_ptr, ctas, iters, stream):
     _check(_lib.mdfft_fp64_rate_probe(c_void_p(out_ptr), int(ctas), int(iters), c_void_p(stream),
                                       ctypes.byref(tf)), "mdfft_fp64_rate_probe")
     return tf.value
+
+
+def mdfft_dist_local_range(plan, step, G, g):
+    x0, x1 = i64(), i64()
+    _check(_lib.mdfft_dist_local_range(plan, int(step), int(G), int(g), ctypes.byref(x0), ctypes.byref(x1)),
+           "mdfft_dist_local_range")
+    return x0.value, x1.value
+
+
+def mdfft_dist_lines(plan, step, G, g, in_ptr, out_ptr, dir, normalize, stream):
+    _check(_lib.mdfft_dist_lines(plan, int(step), int(G), int(g), c_void_p(in_ptr), c_void_p(out_ptr), int(dir),
+                                 int(normalize), c_void_p(stream)), "mdfft_dist_lines")
+
+
+def mdfft_dist_pack(plan, step, G, g, local_ptr, send_ptr, stream):
+    _check(_lib.mdfft_dist_pack(plan, int(step), int(G), int(g), c_void_p(local_ptr), c_void_p(send_ptr),
+                                c_void_p(stream)), "mdfft_dist_pack")
+
+
+def mdfft_dist_unpack(plan, step, G, h, recv_ptr, local_ptr, stream):
+    _check(_lib.mdfft_dist_unpack(plan, int(step), int(G), int(h), c_void_p(recv_ptr), c_void_p(local_ptr),
+                                  c_void_p(stream)), "mdfft_dist_unpack")
 
 
 def mdfft_plan_check(plan):
@@ -649,3 +675,74 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class DistPlan:
+    """Device g's part of a transform whose P virtual processes sit on G
+    devices (torch CUDA tensors).  Every step runs the library's line DFTs,
+    pack and unpack on this device; the values cross devices only through
+    `exchange(send, send_counts, recv_counts) -> recv`, the caller's
+    all-to-all-v (see torch_exchange)."""
+
+    def __init__(self, shape, P, G, g, order=None, dtype="c64"):
+        self.plan = Plan(shape, P, order, dtype)
+        self.M, self.G, self.g = self.plan.M, int(G), int(g)
+
+    def local_range(self, step):
+        return mdfft_dist_local_range(self.plan.handle, step, self.G, self.g)
+
+    def counts(self, step):
+        """G x G points sent from device a (row) to device b (column) at step."""
+        return mdfft_exchange_counts(self.plan.handle, step, self.G)
+
+    def run(self, x_local, exchange, dir=-1, normalize=False, stream=None):
+        """x_local: this device's range of the natural input (layout 0);
+        returns its range of the natural-order result."""
+        import torch
+        st = self.plan._stream(stream)
+        h = self.plan.handle
+        cur = x_local
+        for s in range(self.M):
+            work = torch.empty_like(cur)
+            mdfft_dist_lines(h, s, self.G, self.g, cur.data_ptr(), work.data_ptr(), dir, int(bool(normalize)), st)
+            c = self.counts(s)
+            send_counts = c[self.g]
+            recv_counts = [c[a][self.g] for a in range(self.G)]
+            send = torch.empty(sum(send_counts), dtype=cur.dtype, device=cur.device)
+            mdfft_dist_pack(h, s, self.G, self.g, work.data_ptr(), send.data_ptr(), st)
+            recv = exchange(send, send_counts, recv_counts)
+            x0, x1 = self.local_range(s + 1)
+            nxt = torch.empty(x1 - x0, dtype=cur.dtype, device=cur.device)
+            mdfft_dist_unpack(h, s, self.G, self.g, recv.data_ptr(), nxt.data_ptr(), st)
+            cur = nxt
+        return cur
+
+    def close(self):
+        self.plan.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def torch_exchange(group=None, via_host=False):
+    """An exchange for DistPlan.run over torch.distributed: one
+    all_to_all_single with the step's split sizes (NCCL: grouped send/recv of
+    device buffers into a local receive buffer; via_host=True carries the
+    buffers through host memory, e.g. for the gloo backend)."""
+    import torch
+    import torch.distributed as dist
+
+    def exchange(send, send_counts, recv_counts):
+        src = send.cpu() if via_host else send
+        # complex values travel as (re, im) pairs of reals: two per point
+        src = torch.view_as_real(src).reshape(-1)
+        recv = torch.empty(2 * sum(recv_counts), dtype=src.dtype, device=src.device)
+        dist.all_to_all_single(recv, src, output_split_sizes=[2 * c for c in recv_counts],
+                               input_split_sizes=[2 * c for c in send_counts], group=group)
+        recv = torch.view_as_complex(recv.view(-1, 2))
+        return recv.to(send.device) if via_host else recv
+
+    return exchange
