@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--profile-batch", type=int, default=8, help="volumes per launch in --profile-case")
     ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
     ap.add_argument("--profile-shape", default="256,256,256", help="grid of --profile-case, e.g. 64,64,64,64")
+    ap.add_argument("--profile-tune", action="store_true",
+                    help="--profile-case autotunes the plan first (radix splits included), as the bench's studies do")
     ap.add_argument("--serving-only", type=int, default=0, metavar="REQUESTS",
                     help="run only the serving study with this many requests and print it")
     ap.add_argument("--serving-budget-gb", type=float, default=40.0)
@@ -859,12 +861,13 @@ def precision_study(dev, with_oracle=True):
 
 def profile_case(args):
     """Two forward transforms of a batch of volumes with the planner's best
-    order (M + M pass launches: a warm-up, then the profiled ones)."""
+    order (M + M pass launches: a warm-up, then the profiled ones, inside the
+    NVTX range "profiled"); with --profile-tune the plan is autotuned first."""
     import numpy as np
     import torch
 
     import synth_inputs as si
-    from paper_1302_6189_gb300 import Plan
+    from paper_1302_6189_gb300 import MDFFT_PLAN_TUNE_RADIX, Plan
 
     torch.cuda.set_device(0)
     shape = tuple(int(v) for v in args.profile_shape.split(","))
@@ -874,14 +877,20 @@ def profile_case(args):
                     device="cuda")
     for i in range(B):
         (x[i] if B > 1 else x).copy_(torch.from_numpy(si.uniform_complex(shape, si.SEEDS["cube256"] + i, npdt)))
-    with Plan(shape, args.P, None, args.profile_dtype, batch=B) as plan:
+    flags = MDFFT_PLAN_TUNE_RADIX if args.profile_tune and args.profile_dtype == "c64" else 0
+    with Plan(shape, args.P, None, args.profile_dtype, flags, batch=B) as plan:
         y = torch.empty_like(x)
-        plan.exec(x, y)  # warm-up: launches 1..M
-        plan.exec(x, y)  # profiled: launches M+1..2M
+        if args.profile_tune:
+            plan.autotune(x, y, reps=3)
+        plan.exec(x, y)  # warm-up: launches 1..M (after any autotuning)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        plan.exec(x, y)  # profiled: the next M launches
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         plan.check()
         print(json.dumps({"profile_case": f"{B} x {'x'.join(map(str, shape))} {args.profile_dtype} forward",
-                          "order": plan.order_str(), "passes": plan.describe()}))
+                          "order": plan.order_str(), "tuning": plan.tuning(), "passes": plan.describe()}))
 
 
 def serving_study(dev, n=2000, budget=40e9):

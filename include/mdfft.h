@@ -343,7 +343,8 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * fixed 512-thread CTAs, 3 / 4 persistent pipelined with 1 / 2 landing
  * buffers, 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 /
  * 384-thread CTAs (lengths 24, 48), 8 the alternative radix plan (lengths 32,
- * 48, 64, 96, 128, 160, 192, 256, 512: e.g. 8x8x4 for 256, 8x8x8 for 512);
+ * 48, 64, 96, 128, 160, 192, 256, 512: e.g. 8x8x4 for 256, 8x8x8 for 512),
+ * 9 the default shape capped at the registers of 6 CTAs per SM (24 .. 64);
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,

@@ -683,4 +683,12 @@ __global__ void __launch_bounds__(PassCfg<Real, N, TC, THR, RP>::THREADS) fft_pa
     pass_tile<Real, N, TC, THR, RP>(a, blockIdx.x, smem_raw, threadIdx.x);
 }
 
+// The same kernel with a register cap for MINB resident CTAs per SM (more
+// warps in flight for short lines; some registers spill): an autotuning variant.
+template <int N, int MINB>
+__global__ void __launch_bounds__(PassCfg<float, N>::THREADS, MINB) fft_pass_occ_kernel(const PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pass_tile<float, N, 0, 0, 0>(a, blockIdx.x, smem_raw, threadIdx.x);
+}
+
 }  // namespace mdfft

@@ -980,6 +980,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                     (uintptr_t)out % 16 == 0)
                     variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
+            if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
         }
         if (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) {
             const int tc = p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16;
@@ -1065,11 +1066,14 @@ namespace {
 // The launch variants the autotuner chooses among, by code:
 // 0 default, 1 / 2 fixed 256 / 512-thread CTAs, 3 / 4 pipelined with 1 / 2 landing buffers,
 // 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 / 384-thread CTAs,
-// 8 the alternative radix plan (default CTA shape rule).
-constexpr int kTuningVariants = 9;
+// 8 the alternative radix plan (default CTA shape rule), 9 a register cap for
+// 6 CTAs per SM.
+constexpr int kTuningVariants = 10;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     switch (variant) {
+        case 9:
+            return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_occ(n, k);
         case 8:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_alt(n, k);
         case 6:

@@ -39,4 +39,20 @@ bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k) {
     }
 }
 
+// The default launch shape with a register cap for 6 CTAs per SM (short
+// lines; a few registers spill), an autotuning variant.
+bool find_pass_kernel_c64_occ(int64_t n, PassKernel *k) {
+    switch (n) {
+#define MDFFT_CASE(N)                                                                                       \
+    case N:                                                                                                 \
+        *k = PassKernel{(const void *)&fft_pass_occ_kernel<N, 6>, PassCfg<float, N>::THREADS,               \
+                        PassCfg<float, N>::LINES, PassCfg<float, N>::TL, PassCfg<float, N>::SMEM, PassCfg<float, N>::plan}; \
+        return true;
+        MDFFT_CASE(24) MDFFT_CASE(32) MDFFT_CASE(48) MDFFT_CASE(64)
+#undef MDFFT_CASE
+        default:
+            return false;
+    }
+}
+
 }  // namespace mdfft
