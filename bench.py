@@ -600,9 +600,13 @@ def extra_table(dev, x, P, with_oracle=True):
     # FP64 operations the pass kernel executes, counted by ncu (multiply-adds
     # x 2 + adds + multiplies per launch of one volume), if that count was
     # taken on the current kernel sources
-    counted = profile_values(PROFILE_C128).get("dp_flops_per_launch")
+    prof = profile_values(PROFILE_C128)
+    counted, inst = prof.get("dp_flops_per_launch"), prof.get("dp_inst_per_launch")
     avg_pass_ms = sum(pass_ms) / len(pass_ms)
     counted_tflops = None if counted is None else B * counted / (avg_pass_ms * 1e-3) / 1e12
+    # the FP64 pipe issues one instruction per slot whatever its kind: its
+    # busy fraction is the instruction rate over the multiply-add rate
+    issue_frac = None if inst is None else B * inst / (avg_pass_ms * 1e-3) / (peak64 * 1e12 / 2)
     res["c128"] = {"gbs": round(2 * per_transform / (ms * 1e-3) / 1e9, 1), "ms_per_transform": round(ms / B, 4),
                    "nominal_tflops_fp64": round(fp64_tflops, 3),
                    "pass_ms": [round(v, 4) for v in pass_ms],
@@ -612,6 +616,8 @@ def extra_table(dev, x, P, with_oracle=True):
                                 "achieved": None if counted_tflops is None else round(counted_tflops, 3),
                                 "frac": None if counted_tflops is None else round(counted_tflops / peak64, 3),
                                 "dp_flops_per_launch_per_volume": counted,
+                                "fp64_instructions_per_launch_per_volume": inst,
+                                "fp64_issue_frac": None if issue_frac is None else round(issue_frac, 3),
                                 "achieved_nominal_5TlogT": round(fp64_tflops, 3),
                                 "frac_nominal_work": round(fp64_tflops / peak64, 3)}}
     res["chunk_tile_order"] = chunk_order_study(dev, x, P)
@@ -732,11 +738,11 @@ def md_study(dev, reps=10):
                 out[name] = {"order": format_order(order, M), "comm_points": amount,
                              "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
                              "pass_ms": [round(v, 4) for v in pass_ms], "tuning": tuning,
-                             "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name), B)}
+                             "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name))}
     return out
 
 
-# ncu summaries of single-volume launches of the 4-D / 5-D configurations
+# ncu summaries of the 4-D / 5-D configurations' launches (4 volumes, autotuned plan)
 MD_PROFILES = {"64x64x64x64 P=64 best": os.path.join(ROOT, "profiles", "fft_pass_64x4_c64.md"),
                "24x24x24x24x24 P=64 best": os.path.join(ROOT, "profiles", "fft_pass_24x5_c64.md")}
 
@@ -745,8 +751,8 @@ def pass_roofline(launch_bytes, pass_ms, profile=None, volumes=1):
     """HBM roofline of every pass of a configuration: algorithmic bytes of a
     launch (read + write of the array) over its CUDA-event time, the fraction
     of the measured copy peak, and, when a committed ncu summary of the same
-    kernels holds the DRAM traffic of each pass (one volume per launch), that
-    traffic scaled to the launch over the algorithmic bytes."""
+    kernels holds the DRAM traffic of each pass (`volumes` per launch of the
+    summary), that traffic per launch over the algorithmic bytes."""
     peak, kind = peaks()
     ach = [launch_bytes / (t * 1e-3) / 1e9 for t in pass_ms]
     r = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": kind,

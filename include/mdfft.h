@@ -475,9 +475,10 @@ mdfft_status mdfft_server_drain(mdfft_server_t s);
 mdfft_status mdfft_server_reset_clock(mdfft_server_t s);
 /* Re-captures the graphs with a persistent grid of `ctas` CTAs (autotuning). */
 mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas);
-/* Steps in flight on the GPU at most (1..8, default 2): a step is launched
- * only while fewer are outstanding, so requests arriving meanwhile share the
- * next step instead of each adding nearly empty ones. */
+/* Steps in flight on the GPU at most (1..8, default 2): a batched step is
+ * launched only while fewer are outstanding, so requests arriving meanwhile
+ * share the next step instead of each adding nearly empty ones (low-load
+ * direct steps are not held back). */
 mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth);
 /* At most this many consecutive tiles (1..64, default 4) are dealt to a CTA
  * of the persistent kernel at a time; each step deals chunks of its tile

@@ -448,9 +448,13 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     for (Request *r : s->inflight)
         if (r->next_pass < r->plan->M) todo.push_back(r);
     if (todo.empty()) return MDFFT_OK;
+    // low load: nothing queued and few requests with passes left -- they run
+    // at once (the depth limit, which lets arrivals gather into fuller
+    // steps, does not hold them back)
+    const bool direct = (int)todo.size() <= s->direct && s->queue.empty();
     int busy = 0;
     for (const Slot &b : s->slots) busy += b.busy;
-    if (busy >= s->depth) return MDFFT_OK;  // the GPU has enough queued: let more work gather
+    if (!direct && busy >= s->depth) return MDFFT_OK;  // the GPU has enough queued: let more work gather
     Slot &sl = s->slots[s->next_slot];
     if (sl.busy) {  // its table may still be in use: wait for that step
         cudaError_t e = cudaEventSynchronize(sl.done);
@@ -458,7 +462,7 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         resolve_slot(s, sl);
     }
     cudaError_t e = cudaSuccess;
-    if ((int)todo.size() <= s->direct && s->queue.empty()) {
+    if (direct) {
         // low load: every remaining pass of these requests, oldest first, as
         // plain pass launches (stream order keeps each request's passes in order)
         for (Request *r : todo) {

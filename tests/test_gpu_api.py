@@ -34,6 +34,7 @@ def test_server_run_loop_and_clock():
     xs = [torch.from_numpy(si.uniform_complex(sh, 980 + i, np.complex64)).to(DEV) for i, sh in enumerate(shapes)]
     outs = [torch.empty_like(x) for x in xs]
     with md.Server(budget_bytes=1 << 28, max_inflight=8) as srv:
+        srv.set_direct(0)  # batched steps only: one pass of every request per step
         srv.reset_clock()
         ids = [srv.submit(x, y) for x, y in zip(xs, outs)]
         for _ in range(100):
@@ -45,6 +46,12 @@ def test_server_run_loop_and_clock():
         assert all(t >= 0 for t in times)
         st = srv.stats()
         assert st["completed"] == 3 and st["steps"] >= 4  # a 4-D request needs four steps
+        assert st["direct_requests"] == 0
+    with md.Server(budget_bytes=1 << 28, max_inflight=8) as srv:  # default: low load runs them directly
+        ids = [srv.submit(x, y) for x, y in zip(xs, outs)]
+        srv.drain()
+        st = srv.stats()
+        assert st["completed"] == 3 and st["steps"] == 1 and st["direct_requests"] == 3
     for sh, x, y in zip(shapes, xs, outs):
         with md.Plan(sh, min(64, int(np.prod(sh)))) as pl:
             assert torch.equal(y, pl.exec(x))

@@ -44,6 +44,7 @@ def test_mix_equals_alone_and_oracle():
     outs = [torch.empty_like(x) for x in xs]
     dirs = [int(rng.choice([-1, 1])) for _ in shapes]
     with md.Server(budget_bytes=1 << 30, max_inflight=16, P=64) as srv:
+        srv.set_direct(0)  # every pass through the persistent grouped kernel
         ids = []
         i = 0
         while i < len(shapes):  # arrivals interleaved with steps: requests join mid-flight
@@ -98,6 +99,7 @@ def test_single_cta_grid_and_errors():
     x = torch.from_numpy(si.uniform_complex(shape, 700, np.complex64)).to(DEV)
     y = torch.empty_like(x)
     with md.Server(budget_bytes=1 << 26, max_inflight=4) as srv:
+        srv.set_direct(0)
         srv.set_grid(1)  # one CTA walks every tile
         srv.submit(x, y)
         srv.drain()
