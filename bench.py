@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--profile-batch", type=int, default=8, help="volumes per launch in --profile-case")
     ap.add_argument("--profile-dtype", default="c64", choices=["c64", "c128", "c64_tc_fp16", "c64_tc_bf16"])
     ap.add_argument("--profile-shape", default="256,256,256", help="grid of --profile-case, e.g. 64,64,64,64")
+    ap.add_argument("--profile-tuning", default=None,
+                    help="--profile-case applies this tuning record (JSON: one entry for every pass, or a list)")
     ap.add_argument("--profile-tune", action="store_true",
                     help="--profile-case autotunes the plan first (radix splits included), as the bench's studies do")
     ap.add_argument("--serving-only", type=int, default=0, metavar="REQUESTS",
@@ -815,7 +817,8 @@ PRECISION_BOUNDS = {"c64": 1e-5, "c64_tc_fp16": 1e-5, "c64_tc_bf16": 1e-4, "c128
 def precision_study(dev, with_oracle=True):
     """512^3, N(0,1) re/im (seed 1306), P = 4096, the planner's best order:
     forward transform of the FP32 SIMT path, the tensor-core FP16 / BF16
-    hi-lo paths and the FP64 path.  Throughput (bytes of the M passes) and,
+    hi-lo paths and the FP64 path, each plan autotuned (kernel variant and
+    tiles; results bit-identical to the default launch).  Throughput (bytes of the M passes) and,
     with_oracle, every output element against the FP64 oracle's spectrum of
     the same input: rel-L2 and the largest element error over the RMS, beside
     the stated bound."""
@@ -840,6 +843,8 @@ def precision_study(dev, with_oracle=True):
         xin = x.to(torch.complex128) if dt == "c128" else x
         y = torch.empty_like(xin)
         with Plan(shape, 4096, order, dt) as pl:
+            pl.autotune(xin, y, reps=3)
+            tuning = pl.tuning()
             for _ in range(2):
                 pl.exec(xin, y)
             pl.set_timing(True)
@@ -854,7 +859,8 @@ def precision_study(dev, with_oracle=True):
             pass_ms, _ = pl.pass_times()
         elem = 16 if dt == "c128" else 8
         row = {"gbs": round(per_transform * elem / 8 / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4),
-               "pass_ms": [round(v, 4) for v in pass_ms], "bound_rel_l2": PRECISION_BOUNDS[dt]}
+               "pass_ms": [round(v, 4) for v in pass_ms], "bound_rel_l2": PRECISION_BOUNDS[dt],
+               "tuning": [t["variant"] for t in tuning]}
         if dt != "c128":  # the complex128 path is FP64-bound (see extra.c128)
             row["roofline"] = pass_roofline(2 * T * elem, pass_ms, PRECISION_PROFILES.get(dt))
         if ref is not None:
@@ -888,6 +894,9 @@ def profile_case(args):
         y = torch.empty_like(x)
         if args.profile_tune:
             plan.autotune(x, y, reps=3)
+        if args.profile_tuning:
+            t = json.loads(args.profile_tuning)
+            plan.set_tuning([dict(e) for e in t] if isinstance(t, list) else [dict(t) for _ in shape])
         plan.exec(x, y)  # warm-up: launches 1..M (after any autotuning)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("profiled")

@@ -327,7 +327,8 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * that streams tiles through shared memory with bulk (TMA) copies; a plan
  * using it needs 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).
  * Tensor-core plans (lengths 128, 256, 512) also try 128-thread CTAs (half
- * the lines per tile, more CTAs per SM), and non-persistent kernels the
+ * the lines per tile, more CTAs per SM) and, for 256 and 512, CTAs of two
+ * independent 128-thread groups, and non-persistent kernels the
  * input-chunk tile order (mdfft_pass_info.tile_order).  Plans made with
  * MDFFT_PLAN_TUNE_RADIX (complex64) also try the alternative radix plan of
  * the length (its twiddle table is made again for the chosen plan).  Kernel
@@ -344,7 +345,9 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * buffers, 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 /
  * 384-thread CTAs (lengths 24, 48), 8 the alternative radix plan (lengths 32,
  * 48, 64, 96, 128, 160, 192, 256, 512: e.g. 8x8x4 for 256, 8x8x8 for 512),
- * 9 the default shape capped at the registers of 6 CTAs per SM (24 .. 64);
+ * 9 the default shape capped at the registers of 6 CTAs per SM (24 .. 64),
+ * 10 the tensor-core kernel whose 128-thread groups each walk their own
+ * tiles (lengths 256 and 512; tiles of 8 or 4 lines);
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,

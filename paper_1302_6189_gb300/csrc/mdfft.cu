@@ -985,6 +985,8 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
         if (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) {
             const int tc = p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16;
             if (mdfft::find_pass_kernel_tc_thr(ps.n, tc, 128, &k) && k.fn != ps.k.fn) variants.push_back(k);
+            for (bool land : {true, false})
+                if (mdfft::find_pass_kernel_tcg(ps.n, tc, land, &k) && k.fn != ps.k.fn) variants.push_back(k);
         }
         float best_ms = -1.f, default_ms = -1.f;
         Pass best = ps;
@@ -1067,11 +1069,17 @@ namespace {
 // 0 default, 1 / 2 fixed 256 / 512-thread CTAs, 3 / 4 pipelined with 1 / 2 landing buffers,
 // 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 / 384-thread CTAs,
 // 8 the alternative radix plan (default CTA shape rule), 9 a register cap for
-// 6 CTAs per SM.
-constexpr int kTuningVariants = 10;
+// 6 CTAs per SM, 10 / 11 the tensor-core kernel with independent 128-thread
+// groups, with landing buffers / with first-stage loads from HBM.
+constexpr int kTuningVariants = 12;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     switch (variant) {
+        case 10:
+        case 11:
+            return (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) &&
+                   mdfft::find_pass_kernel_tcg(n, p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16,
+                                               variant == 10, k);
         case 9:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_occ(n, k);
         case 8:

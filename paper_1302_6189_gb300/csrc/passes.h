@@ -40,6 +40,7 @@ bool find_pass_kernel_c64(int64_t n, PassKernel *k);
 bool find_pass_kernel_c128(int64_t n, PassKernel *k);
 bool find_pass_kernel_tc(int64_t n, int tc, PassKernel *k);  // tc: kTcFp16 or kTcBf16
 bool find_pass_kernel_tc_thr(int64_t n, int tc, int thr, PassKernel *k);  // thr: 128-thread CTAs
+bool find_pass_kernel_tcg(int64_t n, int tc, bool land, PassKernel *k);  // independent 128-thread groups (256, 512)
 bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k);  // thr: 256 or 512 threads; 192 or 384 for 24, 48
 bool find_pass_kernel_pipe(int64_t n, int nbuf, PassKernel *k);    // persistent, bulk-copy pipelined
 bool find_pass_kernel_c64_alt(int64_t n, PassKernel *k);           // alternative radix plan (radix_plan_alt)
