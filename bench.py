@@ -723,6 +723,9 @@ def md_study(dev, reps=10):
             for want in (0, 1):
                 order, amount = mdfft_order_search(shape, P, want)
                 with Plan(shape, P, order, "c64", MDFFT_PLAN_TUNE_RADIX, batch=B) as pl:
+                    # the bound the passes' access pattern sets: the same loads and
+                    # transposed stores without the butterflies (default tiles)
+                    pattern_ms = [pl.pattern_probe(s_, x, y, reps=5) for s_ in range(M)]
                     pl.autotune(x, y, reps=3)
                     tuning = [dict(t, radix=d["radix"]) for t, d in zip(pl.tuning(), pl.describe())]
                     for _ in range(3):
@@ -740,6 +743,7 @@ def md_study(dev, reps=10):
                 out[name] = {"order": format_order(order, M), "comm_points": amount,
                              "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
                              "pass_ms": [round(v, 4) for v in pass_ms], "tuning": tuning,
+                             "pattern_bound_gbs": [round(2 * B * T * 8 / (v * 1e-3) / 1e9, 1) for v in pattern_ms],
                              "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name))}
     return out
 
@@ -843,6 +847,7 @@ def precision_study(dev, with_oracle=True):
         xin = x.to(torch.complex128) if dt == "c128" else x
         y = torch.empty_like(xin)
         with Plan(shape, 4096, order, dt) as pl:
+            pattern_ms = [pl.pattern_probe(s_, xin, y, reps=3) for s_ in range(3)] if dt == "c64" else None
             pl.autotune(xin, y, reps=3)
             tuning = pl.tuning()
             for _ in range(2):
@@ -863,6 +868,8 @@ def precision_study(dev, with_oracle=True):
                "tuning": [t["variant"] for t in tuning]}
         if dt != "c128":  # the complex128 path is FP64-bound (see extra.c128)
             row["roofline"] = pass_roofline(2 * T * elem, pass_ms, PRECISION_PROFILES.get(dt))
+        if pattern_ms:
+            row["pattern_bound_gbs"] = [round(2 * T * 8 / (v * 1e-3) / 1e9, 1) for v in pattern_ms]
         if ref is not None:
             row.update(errors_vs(y.cpu().numpy(), ref))
             row["within_bound"] = row["rel_l2"] <= PRECISION_BOUNDS[dt]

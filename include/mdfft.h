@@ -346,8 +346,12 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * 384-thread CTAs (lengths 24, 48), 8 the alternative radix plan (lengths 32,
  * 48, 64, 96, 128, 160, 192, 256, 512: e.g. 8x8x4 for 256, 8x8x8 for 512),
  * 9 the default shape capped at the registers of 6 CTAs per SM (24 .. 64),
- * 10 the tensor-core kernel whose 128-thread groups each walk their own
- * tiles (lengths 256 and 512; tiles of 8 or 4 lines);
+ * 10 / 11 the tensor-core kernel whose 128-thread groups each walk their
+ * own tiles (lengths 256 and 512; tiles of 8 or 4 lines), with landing
+ * buffers / loading the first stage from HBM, 12 / 13 a persistent complex64
+ * kernel that loads the next tile's first-stage inputs into registers while
+ * the current tile runs (lengths 24, 32, 48, 64; registers for 2 / 4 CTAs
+ * per SM), 14 / 15 the same with the alternative radix plan (64);
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,
@@ -368,7 +372,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *ou
  * same loads, the same transposed stores into the next layout) but does no
  * butterflies, and returns its mean duration in ms.  Its bandwidth is the
  * bound the redistribution's access pattern puts on the pass.  complex64
- * plans and line lengths 32, 48, 64, 96, 128, 160, 192, 256, 512 only
+ * plans and line lengths 24, 32, 48, 64, 96, 128, 160, 192, 256, 512 only
  * (E_UNSUPPORTED otherwise).  in_dev is read, out_dev overwritten (T
  * elements each); synchronises the stream.
  */

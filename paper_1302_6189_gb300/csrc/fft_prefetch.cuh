@@ -1,0 +1,132 @@
+// fft_prefetch.cuh -- persistent complex64 pass kernel that loads the next
+// tile's first-stage inputs into registers while the current tile is
+// transformed and stored (short lines, where a tile's work between its HBM
+// loads and its barriers is small).
+//
+// The same pass as fft_pass_kernel (Fig. 4 step + the transpose after it),
+// same tiles, stages and store; each CTA walks tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (the host launches one resident wave).  At the
+// top of tile t every thread issues the loads of its first-stage butterflies
+// of tile t + gridDim.x; they are consumed one tile later, so their latency
+// overlaps tile t.  The twiddles are staged once per CTA.  MINB: CTAs per SM
+// the register allocation must allow (2: no spills, 4: a few spilled bytes).
+#pragma once
+
+#include "fft_pass.cuh"
+
+namespace mdfft {
+
+template <int N, int RP = 0> struct PfCfg {
+    using Cfg = PassCfg<float, N, 0, 0, RP>;
+    static_assert(Cfg::DIRECT, "the first stage must read HBM directly");
+    static constexpr int R0 = Cfg::plan.R[0];
+    static constexpr int NB0 = N / R0;
+    static constexpr int PER0 = (NB0 + Cfg::TL - 1) / Cfg::TL;
+    static constexpr bool SINGLE = Cfg::plan.S == 1;
+    // two sets of tile coordinates and line offsets (tile parity)
+    static constexpr size_t SMEM = Cfg::SMEM + (size_t)(Cfg::LINES + 4) * sizeof(int64_t);
+};
+
+// Input offset of this thread's line in tile t, and whether the line exists.
+template <int N, int RP>
+__device__ __forceinline__ bool pf_line(const PassArgs &a, int64_t t, int line, int64_t *base) {
+    const TileCoord c = tile_coords(a, t);
+    const int bg = line % a.Bg, bh = line / a.Bg;
+    *base = c.in_base + bg * a.in_sg + bh * a.in_sh;
+    return line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
+}
+
+template <int N, int RP>
+__device__ __forceinline__ void pf_load(const float2 *in, int64_t base, bool ok, int tl, bool conj,
+                                        float2 (&v)[PfCfg<N, RP>::PER0][PfCfg<N, RP>::R0]) {
+    using P = PfCfg<N, RP>;
+    using Cfg = typename P::Cfg;
+#pragma unroll
+    for (int i = 0; i < P::PER0; ++i) {
+        const int j = tl + i * Cfg::TL;
+#pragma unroll
+        for (int r = 0; r < P::R0; ++r) {
+            float2 x = make_float2(0.f, 0.f);
+            if ((P::NB0 % Cfg::TL == 0 || j < P::NB0) && ok) x = __ldg(in + base + j + r * P::NB0);
+            if (conj) x.y = -x.y;
+            v[i][r] = x;
+        }
+    }
+}
+
+template <int N, int RP = 0, int MINB = 2>
+__global__ void __launch_bounds__(PassCfg<float, N, 0, 0, RP>::THREADS, MINB) fft_pass_pf_kernel(const PassArgs a) {
+    using P = PfCfg<N, RP>;
+    using Cfg = typename P::Cfg;
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char pf_smem[];
+    C *buf = reinterpret_cast<C *>(pf_smem);  // stage buffer / transposed tile
+    C *tw = buf + Cfg::DATA;
+    int64_t *sets = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);  // 2 x (line offsets, tile coordinates)
+    const int tid = threadIdx.x;
+    const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
+    const C *in = reinterpret_cast<const C *>(a.in);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+    const bool conj = (a.conj & 1) != 0;
+    for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
+
+    __syncthreads();  // the twiddles before any stage reads them
+    const int64_t G = gridDim.x;
+    int64_t t = blockIdx.x;
+    C cur[P::PER0][P::R0], nxt[P::PER0][P::R0];
+    int64_t base = 0;
+    bool ok = false;
+    if (t < a.ntiles) {
+        ok = pf_line<N, RP>(a, t, line, &base);
+        pf_load<N, RP>(in, base, ok, tl, conj, cur);
+    }
+    for (int par = 0; t < a.ntiles; t += G, par ^= 1) {
+        const bool fok = ok;
+        // the next tile's inputs: in flight while this tile is computed and stored
+        if (t + G < a.ntiles) {
+            ok = pf_line<N, RP>(a, t + G, line, &base);
+            pf_load<N, RP>(in, base, ok, tl, conj, nxt);
+        }
+        int64_t *lbase = sets + par * (Cfg::LINES + 4);
+        TileCoord *shc = reinterpret_cast<TileCoord *>(lbase + Cfg::LINES);
+        if (tid < 32) {
+            const TileCoord w0 = tile_coords(a, t);
+            if (tid == 0) *shc = w0;
+            for (int l = tid; l < Cfg::LINES; l += 32) {
+                const int bg = l % a.Bg, bh = l / a.Bg;
+                lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
+            }
+        }
+        // the first stage (no twiddles) from the registers (the previous
+        // tile's store finished reading the buffer at the end of its iteration)
+        constexpr int R = P::R0, NB = P::NB0;
+#pragma unroll
+        for (int i = 0; i < P::PER0; ++i) {
+            const int j = tl + i * Cfg::TL;
+            if ((NB % Cfg::TL == 0 || j < NB) && fok) {
+                dft<R>(cur[i]);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if constexpr (P::SINGLE) buf[(j * R + r) * Cfg::TROW + line] = cur[i][r];
+                    else buf[line * Cfg::PADN + padg<Cfg::PADG>(j * R + r)] = cur[i][r];
+                }
+            }
+        }
+        if constexpr (P::SINGLE) {
+            __syncthreads();
+        } else {
+            constexpr bool WARP_LOCAL = 32 % Cfg::TL == 0;
+            if constexpr (WARP_LOCAL && Cfg::plan.S > 1) __syncwarp();
+            else __syncthreads();
+            Stages<float, N, 1, R, 0, 0, -1, RP>::run(buf, buf, tw, nullptr, line, tl, fok, false, true);
+        }
+        store_tile<float, N, 0, 0, RP>(a, buf, lbase, *shc, tid);
+        __syncthreads();  // the buffer is rewritten by the next tile's first stage
+#pragma unroll
+        for (int i = 0; i < P::PER0; ++i)
+#pragma unroll
+            for (int r = 0; r < R; ++r) cur[i][r] = nxt[i][r];
+    }
+}
+
+}  // namespace mdfft

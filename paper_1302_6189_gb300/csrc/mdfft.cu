@@ -981,6 +981,9 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                     variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
+            for (int rp = 0; rp < ((p->flags & MDFFT_PLAN_TUNE_RADIX) ? 2 : 1); ++rp)
+                for (int minb : {2, 4})
+                    if (mdfft::find_pass_kernel_c64_pf(ps.n, rp, minb, &k)) variants.push_back(k);
         }
         if (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) {
             const int tc = p->dt == MDFFT_C64_TC_FP16 ? mdfft::kTcFp16 : mdfft::kTcBf16;
@@ -1070,11 +1073,19 @@ namespace {
 // 5 tensor-core kernel with 128-thread CTAs, 6 / 7 fixed 192 / 384-thread CTAs,
 // 8 the alternative radix plan (default CTA shape rule), 9 a register cap for
 // 6 CTAs per SM, 10 / 11 the tensor-core kernel with independent 128-thread
-// groups, with landing buffers / with first-stage loads from HBM.
-constexpr int kTuningVariants = 12;
+// groups, with landing buffers / with first-stage loads from HBM, 12 / 13 the
+// persistent kernel with the next tile's loads in registers (2 / 4 CTAs per
+// SM), 14 / 15 the same with the alternative radix plan.
+constexpr int kTuningVariants = 16;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     switch (variant) {
+        case 12:
+        case 13:
+        case 14:
+        case 15:
+            return p->dt == MDFFT_C64 &&
+                   mdfft::find_pass_kernel_c64_pf(n, variant >= 14 ? 1 : 0, (variant & 1) ? 4 : 2, k);
         case 10:
         case 11:
             return (p->dt == MDFFT_C64_TC_FP16 || p->dt == MDFFT_C64_TC_BF16) &&

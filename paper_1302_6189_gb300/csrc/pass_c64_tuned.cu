@@ -3,6 +3,7 @@
 // lines of 4 threads) for 24 and 48: the autotuner's alternatives to the
 // default launch shape of pass_c64.cu.  (48 and 96 lines tile axes whose
 // extent is a multiple of 3, e.g. 24 x 2 lines, without idle lines.)
+#include "fft_prefetch.cuh"
 #include "passes.h"
 
 namespace mdfft {
@@ -33,6 +34,35 @@ bool find_pass_kernel_c64_thr(int64_t n, int thr, PassKernel *k) {
         *k = thr == 256 ? make_c64_thr<N, 256>() : make_c64_thr<N, 512>();      \
         return true;
         MDFFT_TUNED_LENGTHS(MDFFT_CASE)
+#undef MDFFT_CASE
+        default:
+            return false;
+    }
+}
+
+// Persistent kernel with the next tile's first-stage loads in registers
+// (fft_prefetch.cuh), for short lines; rp selects the radix plan.
+template <int N, int RP, int MINB> static PassKernel make_pf() {
+    using Cfg = PassCfg<float, N, 0, 0, RP>;
+    PassKernel k{(const void *)&fft_pass_pf_kernel<N, RP, MINB>, Cfg::THREADS, Cfg::LINES, Cfg::TL,
+                 PfCfg<N, RP>::SMEM, Cfg::plan};
+    k.persistent = 1;
+    return k;
+}
+
+bool find_pass_kernel_c64_pf(int64_t n, int rp, int minb, PassKernel *k) {
+    if (minb != 2 && minb != 4) return false;
+    if (rp == 1) {
+        if (n != 64) return false;
+        *k = minb == 2 ? make_pf<64, 1, 2>() : make_pf<64, 1, 4>();
+        return true;
+    }
+    switch (n) {
+#define MDFFT_CASE(N)                                               \
+    case N:                                                         \
+        *k = minb == 2 ? make_pf<N, 0, 2>() : make_pf<N, 0, 4>();   \
+        return true;
+        MDFFT_CASE(24) MDFFT_CASE(32) MDFFT_CASE(48) MDFFT_CASE(64)
 #undef MDFFT_CASE
         default:
             return false;

@@ -58,7 +58,7 @@ bool find_move_kernel_c64(int64_t n, PassKernel *k) {
     case N:                  \
         *k = make_move<N>(); \
         return true;
-        MDFFT_TUNED_LENGTHS(MDFFT_CASE)
+        MDFFT_TUNED_LENGTHS(MDFFT_CASE) MDFFT_CASE(24)
 #undef MDFFT_CASE
         default:
             return false;

@@ -196,7 +196,8 @@ def mdfft_selftest_wait(arrive, limit_us):
     return st, waited.value
 
 
-TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384", "radix_alt", "occ6", "tcg", "tcg_direct")
+TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384", "radix_alt", "occ6", "tcg", "tcg_direct", "pf2", "pf4",
+                   "pf2_radix_alt", "pf4_radix_alt")
 
 
 def mdfft_plan_tuning(plan, M):

@@ -334,7 +334,7 @@ def test_autotune_keeps_results_bit_identical():
             assert all(b <= a * 1.05 + 1e-3 for a, b in zip(ms0, ms1))  # never picks a slower configuration
             after = plan.exec(x)
             torch.cuda.synchronize()
-            if any(t["variant"] == "radix_alt" for t in plan.tuning()):  # another radix split: rounding only
+            if any("radix_alt" in t["variant"] for t in plan.tuning()):  # another radix split: rounding only
                 check(after.cpu().numpy(), oracle.fftn(x.cpu().numpy().astype(np.complex128)), dt, str(shape))
             else:
                 assert torch.equal(before, after), shape

@@ -82,7 +82,7 @@ def test_every_tuning_variant_gives_the_default_bits(shape, P, dt):
                     assert d["tile_order"] == order
                     tried += 1
                     y = pl.exec(x)
-                    if v == "radix_alt":  # another radix split: the same spectrum up to rounding
+                    if "radix_alt" in v:  # another radix split: the same spectrum up to rounding
                         assert d["radix"] != pl_default_radix[s]
                         assert rel_l2(y, want) <= 1e-6, (v, s, d)
                     else:
@@ -93,7 +93,7 @@ def test_every_tuning_variant_gives_the_default_bits(shape, P, dt):
         y = torch.empty_like(x)
         pl.autotune(x, y, reps=2)
         got = pl.exec(x)
-        if any(t["variant"] == "radix_alt" for t in pl.tuning()):
+        if any("radix_alt" in t["variant"] for t in pl.tuning()):
             assert rel_l2(got, want) <= 1e-6
         else:
             assert torch.equal(got, want)
