@@ -351,7 +351,9 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * buffers / loading the first stage from HBM, 12 / 13 a persistent complex64
  * kernel that loads the next tile's first-stage inputs into registers while
  * the current tile runs (lengths 24, 32, 48, 64; registers for 2 / 4 CTAs
- * per SM), 14 / 15 the same with the alternative radix plan (64);
+ * per SM), 14 / 15 the same with the alternative radix plan (64), 16 the
+ * 256-point kernel that exchanges values between its two radix-16 stages
+ * with warp shuffles instead of shared memory;
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,

@@ -130,3 +130,77 @@ __global__ void __launch_bounds__(PassCfg<float, N, 0, 0, RP>::THREADS, MINB) ff
 }
 
 }  // namespace mdfft
+
+namespace mdfft {
+
+// 256-point lines (radix 16 x 16, 16 threads per line) with the exchange
+// between the two stages done in registers: after the first stage, thread j
+// of a line holds y[16 j + q], q = 0..15, and the second stage's butterfly j
+// needs y[16 r + j], r = 0..15 -- a 16 x 16 transpose across the line's 16
+// lanes, done in four XOR steps of warp shuffles (step m swaps, between lanes
+// j and j ^ m, the elements whose index differs from the lane in bit m).  No
+// shared memory between the stages; the second stage writes the transposed
+// tile and the store is unchanged.  An autotuning variant.
+__global__ void __launch_bounds__(PassCfg<float, 256>::THREADS, 4) fft_pass_shfl256_kernel(const PassArgs a) {
+    using Cfg = PassCfg<float, 256>;
+    using C = float2;
+    static_assert(Cfg::TL == 16 && Cfg::plan.S == 2 && Cfg::plan.R[0] == 16 && Cfg::plan.R[1] == 16, "256 = 16 x 16");
+    extern __shared__ __align__(16) unsigned char sh_smem[];
+    C *buf = reinterpret_cast<C *>(sh_smem);  // transposed tile [k][TROW]
+    C *tw = buf + Cfg::DATA;
+    int64_t *lbase = reinterpret_cast<int64_t *>(tw + Cfg::TWN + Cfg::BFRAG);
+    TileCoord *shc = reinterpret_cast<TileCoord *>(lbase + Cfg::LINES);
+    const int tid = threadIdx.x;
+    const C *in = reinterpret_cast<const C *>(a.in);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+    if (tid < 32) {
+        const TileCoord w0 = tile_coords(a, blockIdx.x);
+        if (tid == 0) *shc = w0;
+        for (int l = tid; l < Cfg::LINES; l += 32) {
+            const int bg = l % a.Bg, bh = l / a.Bg;
+            lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
+        }
+    }
+    for (int q = tid; q < tw_entries(Cfg::plan); q += Cfg::THREADS) tw[q] = gtw[q];
+    __syncthreads();
+    const TileCoord c = *shc;
+    const int line = tid / 16, j = tid % 16;
+    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    const bool ok = line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh;
+    C v[16];
+    const C *src = in + lbase[line];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        C x = ok ? __ldg(src + j + 16 * r) : C{0, 0};
+        if (a.conj & 1) x.y = -x.y;
+        v[r] = x;
+    }
+    dft<16>(v);  // v[q] = y[16 j + q]
+    // transpose across the line's 16 lanes: afterwards v[r] = y[16 r + j]
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) {
+        const bool hi = (j & m) != 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i & m) continue;
+            const C send = hi ? v[i] : v[i | m];
+            C got;
+            got.x = __shfl_xor_sync(0xffffffffu, send.x, m);
+            got.y = __shfl_xor_sync(0xffffffffu, send.y, m);
+            if (hi) v[i] = got;
+            else v[i | m] = got;
+        }
+    }
+    // second stage: twiddles w_256^{j r}, DFT-16, results to the transposed tile
+    constexpr int TWOFF = tw_offset(Cfg::plan, 1);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[TWOFF + r * 16 + j]);
+    dft<16>(v);
+    if (ok)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[(j + 16 * q) * Cfg::TROW + line] = v[q];
+    __syncthreads();
+    store_tile<float, 256, 0, 0>(a, buf, lbase, c, tid);
+}
+
+}  // namespace mdfft

@@ -981,6 +981,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                     variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
+            if (mdfft::find_pass_kernel_c64_shfl(ps.n, &k)) variants.push_back(k);
             for (int rp = 0; rp < ((p->flags & MDFFT_PLAN_TUNE_RADIX) ? 2 : 1); ++rp)
                 for (int minb : {2, 4})
                     if (mdfft::find_pass_kernel_c64_pf(ps.n, rp, minb, &k)) variants.push_back(k);
@@ -1075,11 +1076,14 @@ namespace {
 // 6 CTAs per SM, 10 / 11 the tensor-core kernel with independent 128-thread
 // groups, with landing buffers / with first-stage loads from HBM, 12 / 13 the
 // persistent kernel with the next tile's loads in registers (2 / 4 CTAs per
-// SM), 14 / 15 the same with the alternative radix plan.
-constexpr int kTuningVariants = 16;
+// SM), 14 / 15 the same with the alternative radix plan, 16 the 256-point
+// kernel with a warp-shuffle exchange between its two stages.
+constexpr int kTuningVariants = 17;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     switch (variant) {
+        case 16:
+            return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_shfl(n, k);
         case 12:
         case 13:
         case 14:

@@ -69,6 +69,13 @@ bool find_pass_kernel_c64_pf(int64_t n, int rp, int minb, PassKernel *k) {
     }
 }
 
+bool find_pass_kernel_c64_shfl(int64_t n, PassKernel *k) {
+    if (n != 256) return false;
+    using Cfg = PassCfg<float, 256>;
+    *k = PassKernel{(const void *)&fft_pass_shfl256_kernel, Cfg::THREADS, Cfg::LINES, Cfg::TL, Cfg::SMEM, Cfg::plan};
+    return true;
+}
+
 // The default launch shape with a register cap for 6 CTAs per SM (short
 // lines; a few registers spill), an autotuning variant.
 bool find_pass_kernel_c64_occ(int64_t n, PassKernel *k) {

@@ -46,6 +46,7 @@ bool find_pass_kernel_pipe(int64_t n, int nbuf, PassKernel *k);    // persistent
 bool find_pass_kernel_c64_alt(int64_t n, PassKernel *k);           // alternative radix plan (radix_plan_alt)
 bool find_pass_kernel_c64_occ(int64_t n, PassKernel *k);           // register cap for 6 CTAs per SM (24..64)
 bool find_pass_kernel_c64_pf(int64_t n, int rp, int minb, PassKernel *k);  // persistent, next tile's loads in registers
+bool find_pass_kernel_c64_shfl(int64_t n, PassKernel *k);          // 256: warp-shuffle exchange between the stages
 bool find_move_kernel_c64(int64_t n, PassKernel *k);               // data movement of a pass, no FFT
 
 }  // namespace mdfft
