@@ -364,3 +364,24 @@ def test_six_to_eight_dims_with_the_heuristic_order(shape):
         check(y, oracle.fftn(x), dt, str(shape))
         yi, _ = run(shape, 5, None, dt, x, dir=+1, normalize=True)
         check(yi * 1.0, oracle.fftn(x, sign=+1) / x.size, dt, "inverse " + str(shape))
+
+
+@pytest.mark.parametrize("shape,P,B", [((256, 256, 256), 4096, 8), ((64, 64, 64, 64), 64, 4), ((24, 24, 24, 24, 24), 64, 4)])
+def test_benchmark_launch_configurations_against_the_oracle(shape, P, B):
+    # the launches the benchmark times: a batched plan of B volumes, autotuned
+    # with radix splits allowed (kernel variant, tiles, tile order, radix plan
+    # per pass); the first and the last volume of the batch, every element,
+    # against the oracle, and the normalised inverse back to the input
+    vols = [si.uniform_complex(shape, 1303 + i) for i in (0, B - 1)]
+    x = torch.empty((B,) + shape, dtype=torch.complex64, device=DEV)
+    for i in range(B):
+        src = vols[0] if i == 0 else vols[1] if i == B - 1 else si.uniform_complex(shape, 1303 + i)
+        x[i].copy_(torch.from_numpy(src.astype(np.complex64)))
+    with md.Plan(shape, P, None, "c64", md.MDFFT_PLAN_TUNE_RADIX, batch=B) as plan:
+        plan.autotune(x, torch.empty_like(x), reps=2)
+        y = plan.exec(x)
+        back = plan.exec(y, dir=+1, normalize=True)
+        torch.cuda.synchronize()
+        for i, v in ((0, vols[0]), (B - 1, vols[1])):
+            check(y[i].cpu().numpy(), oracle.fftn(v, nthreads=NTH), "c64", f"{shape} volume {i}")
+            check(back[i].cpu().numpy(), v, "c64", f"{shape} round trip {i}")
