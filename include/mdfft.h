@@ -487,7 +487,7 @@ mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas);
 /* Steps in flight on the GPU at most (1..8, default 2): a batched step is
  * launched only while fewer are outstanding, so requests arriving meanwhile
  * share the next step instead of each adding nearly empty ones (low-load
- * direct steps are not held back). */
+ * direct steps are held back only while batched steps are in flight). */
 mdfft_status mdfft_server_set_depth(mdfft_server_t s, int depth);
 /* At most this many consecutive tiles (1..64, default 4) are dealt to a CTA
  * of the persistent kernel at a time; each step deals chunks of its tile

@@ -208,6 +208,7 @@ struct Slot {
     cudaGraphNode_t copy = nullptr;  // the table copy node (its size follows the step's item count)
     cudaEvent_t done = nullptr;
     bool busy = false;
+    bool direct = false;  // the step ran plain pass launches (low load)
     std::vector<Request *> finishing;
 };
 
@@ -449,12 +450,12 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         if (r->next_pass < r->plan->M) todo.push_back(r);
     if (todo.empty()) return MDFFT_OK;
     // low load: nothing queued and few requests with passes left -- they run
-    // at once (the depth limit, which lets arrivals gather into fuller
-    // steps, does not hold them back)
+    // at once; the depth limit, which lets arrivals gather into fuller
+    // steps, holds them back only while batched steps are in flight
     const bool direct = (int)todo.size() <= s->direct && s->queue.empty();
-    int busy = 0;
-    for (const Slot &b : s->slots) busy += b.busy;
-    if (!direct && busy >= s->depth) return MDFFT_OK;  // the GPU has enough queued: let more work gather
+    int busy = 0, busy_batched = 0;
+    for (const Slot &b : s->slots) busy += b.busy, busy_batched += b.busy && !b.direct;
+    if (busy >= s->depth && (!direct || busy_batched > 0)) return MDFFT_OK;  // let more work gather
     Slot &sl = s->slots[s->next_slot];
     if (sl.busy) {  // its table may still be in use: wait for that step
         cudaError_t e = cudaEventSynchronize(sl.done);
@@ -483,6 +484,7 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         e = cudaEventRecord(sl.done, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         sl.busy = true;
+        sl.direct = true;
         s->next_slot = (s->next_slot + 1) % kSlots;
         s->stats.steps++;
         if (launched) *launched = 1;
@@ -541,6 +543,7 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     e = cudaEventRecord(sl.done, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     sl.busy = true;
+    sl.direct = false;
     s->next_slot = (s->next_slot + 1) % kSlots;
     s->stats.steps++;
     if (launched) *launched = 1;
