@@ -623,6 +623,7 @@ def extra_table(dev, x, P, with_oracle=True):
                                 "achieved_nominal_5TlogT": round(fp64_tflops, 3),
                                 "frac_nominal_work": round(fp64_tflops / peak64, 3)}}
     res["chunk_tile_order"] = chunk_order_study(dev, x, P)
+    res["distributed_256cubed"] = dist_study(dev, x[0], P)
     res["small_32cubed_c128"] = small_study(dev)
     res["precision_512cubed"] = precision_study(dev, with_oracle)
     res["md_4d_5d"] = md_study(dev)
@@ -663,6 +664,84 @@ def chunk_order_study(dev, x, P, reps=10):
                          "ctas": [d["ctas"] for d in pl.describe()], "store_axis": [d["store_axis"] for d in pl.describe()],
                          "same_bits": bool(torch.equal(y, want))}
         pl.set_tuning(base)
+    return out
+
+
+def dist_study(dev, x0, P, reps=5):
+    """The data plane of the distributed setting on one GPU: 256^3 complex64,
+    P = 4096, the P processes on G = 2 and 8 virtual devices.  Per order (best
+    and worst), the points that would cross devices per transform (the
+    off-diagonal exchange counts, what a network would carry) beside the
+    order's amount; and, for the best order, the device time of the library's
+    line DFTs, pack and unpack per transform summed over the devices (the
+    transport between them, a copy here, is not timed)."""
+    import torch
+
+    from paper_1302_6189_gb300 import (DistPlan, mdfft_dist_lines, mdfft_dist_pack, mdfft_dist_unpack,
+                                       mdfft_order_search, format_order)
+
+    _, T = algorithmic_bytes(SHAPE, 8)
+    out = {"note": "cross-device points from mdfft_exchange_counts; times: CUDA events, library kernels only"}
+    flat = x0.reshape(-1)
+    for G in (2, 8):
+        row = {}
+        for want in (0, 1):
+            order, amount = mdfft_order_search(SHAPE, P, want)
+            parts = [DistPlan(SHAPE, P, G, g, order) for g in range(G)]
+            try:
+                cross = 0
+                for s_ in range(3):
+                    c = parts[0].counts(s_)
+                    cross += sum(c[a][b] for a in range(G) for b in range(G) if a != b)
+                entry = {"order": format_order(order, 3), "amount": amount, "cross_device_points": cross}
+                if want == 0:
+                    st = torch.cuda.current_stream(dev).cuda_stream
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                    t = {"lines": 0.0, "pack": 0.0, "unpack": 0.0}
+                    for _ in range(reps):
+                        local = []
+                        for g in range(G):
+                            a, b = parts[g].local_range(0)
+                            local.append(flat[a:b].clone())
+                        for s_ in range(3):
+                            c = parts[0].counts(s_)
+                            work = [torch.empty_like(v) for v in local]
+                            sends = [torch.empty(sum(c[g]), dtype=x0.dtype, device=dev) for g in range(G)]
+                            ev[0].record()
+                            for g in range(G):
+                                mdfft_dist_lines(parts[g].plan.handle, s_, G, g, local[g].data_ptr(), work[g].data_ptr(),
+                                                 -1, 0, st)
+                            ev[1].record()
+                            for g in range(G):
+                                mdfft_dist_pack(parts[g].plan.handle, s_, G, g, work[g].data_ptr(), sends[g].data_ptr(), st)
+                            ev[2].record()
+                            recvs = [torch.cat([sends[g][sum(c[g][:h]):sum(c[g][:h + 1])] for g in range(G)])
+                                     for h in range(G)]
+                            nxt = []
+                            for h in range(G):
+                                a, b = parts[h].local_range(s_ + 1)
+                                nxt.append(torch.empty(b - a, dtype=x0.dtype, device=dev))
+                            ev[3].record()
+                            for h in range(G):
+                                mdfft_dist_unpack(parts[h].plan.handle, s_, G, h, recvs[h].data_ptr(), nxt[h].data_ptr(), st)
+                            end = torch.cuda.Event(enable_timing=True)
+                            end.record()
+                            torch.cuda.synchronize(dev)
+                            t["lines"] += ev[0].elapsed_time(ev[1])
+                            t["pack"] += ev[1].elapsed_time(ev[2])
+                            t["unpack"] += ev[3].elapsed_time(end)
+                            local = nxt
+                    per = {k: v / reps for k, v in t.items()}
+                    entry["ms_per_transform"] = {k: round(v, 4) for k, v in per.items()}
+                    # each kernel reads and writes the whole array once per step (3 steps)
+                    entry["gbs"] = {k: round(3 * 2 * T * 8 / (v * 1e-3) / 1e9, 1) for k, v in per.items()}
+                row["best" if want == 0 else "worst"] = entry
+            finally:
+                for p_ in parts:
+                    p_.close()
+        row["worst_over_best_cross_device"] = round(row["worst"]["cross_device_points"] /
+                                                    max(1, row["best"]["cross_device_points"]), 3)
+        out[f"G={G}"] = row
     return out
 
 

@@ -43,27 +43,79 @@ struct CopyBox {
     int64_t ext[kMaxTileDims], src_stride[kMaxTileDims], dst_stride[kMaxTileDims];
 };
 
-template <typename C>
-__global__ void __launch_bounds__(256) box_copy_kernel(const C *__restrict__ src, C *__restrict__ dst,
-                                                      const CopyBox *__restrict__ boxes, int nboxes, int M,
-                                                      int64_t total) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+// Each CTA copies one contiguous range of the copy's points, its threads
+// striding through it, so a thread's box only moves forward: one search at
+// the start, then a step to the next box when its point passes the current
+// one's end.  Coordinates are split in 32-bit arithmetic when every box is
+// smaller than 2^32 points (small32), else in 64-bit.  A thread works on
+// kUnroll points at a time: all their loads are in flight before the stores.
+template <typename C> struct BoxWalk {
+    const CopyBox *boxes;
+    int nboxes, M, small32, cur;
+    int64_t total, next;
+    __device__ __forceinline__ void seek(int64_t e) {
         int lo = 0, hi = nboxes - 1;  // last box starting at or before e
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (boxes[mid].start <= e) lo = mid;
             else hi = mid - 1;
         }
-        const CopyBox &b = boxes[lo];
-        int64_t r = e - b.start, s = b.src_base, d = b.dst_base;
-        for (int i = M - 1; i >= 0; --i) {
-            const int64_t c = r % b.ext[i];
-            r /= b.ext[i];
-            s += c * b.src_stride[i];
-            d += c * b.dst_stride[i];
+        cur = lo;
+        next = cur + 1 < nboxes ? boxes[cur + 1].start : total;
+    }
+    // source and destination index of point e (e only grows between calls)
+    __device__ __forceinline__ void at(int64_t e, int64_t &s, int64_t &d) {
+        while (e >= next) {
+            ++cur;
+            next = cur + 1 < nboxes ? boxes[cur + 1].start : total;
         }
-        dst[d] = src[s];
+        const CopyBox &b = boxes[cur];
+        s = b.src_base, d = b.dst_base;
+        if (small32) {
+            uint32_t r = (uint32_t)(e - b.start);
+            for (int i = M - 1; i >= 0 && r; --i) {
+                const uint32_t x = (uint32_t)b.ext[i], c = r % x;
+                r /= x;
+                s += (int64_t)c * b.src_stride[i];
+                d += (int64_t)c * b.dst_stride[i];
+            }
+        } else {
+            int64_t r = e - b.start;
+            for (int i = M - 1; i >= 0 && r; --i) {
+                const int64_t c = r % b.ext[i];
+                r /= b.ext[i];
+                s += c * b.src_stride[i];
+                d += c * b.dst_stride[i];
+            }
+        }
+    }
+};
+
+constexpr int kUnroll = 4;
+
+template <typename C>
+__global__ void __launch_bounds__(256) box_copy_kernel(const C *__restrict__ src, C *__restrict__ dst,
+                                                      const CopyBox *__restrict__ boxes, int nboxes, int M,
+                                                      int64_t total, int64_t per_cta, int small32) {
+    const int64_t e0 = (int64_t)blockIdx.x * per_cta;
+    const int64_t e1 = e0 + per_cta < total ? e0 + per_cta : total;
+    int64_t e = e0 + threadIdx.x;
+    if (e >= e1) return;
+    BoxWalk<C> w{boxes, nboxes, M, small32, 0, total, 0};
+    w.seek(e);
+    const int64_t step = blockDim.x;
+    for (; e < e1; e += kUnroll * step) {
+        int64_t si[kUnroll], di[kUnroll];
+        C v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (e + u * step < e1) w.at(e + u * step, si[u], di[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (e + u * step < e1) v[u] = src[si[u]];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (e + u * step < e1) dst[di[u]] = v[u];
     }
 }
 
@@ -161,7 +213,7 @@ mdfft_status make_boxes(const mdfft_plan_s *p, int step, int G, int me, bool pac
     return MDFFT_OK;
 }
 
-mdfft_status check_dist(const mdfft_plan_s *p, int step, int G, int g, bool exchange) {
+mdfft_status check_dist(const mdfft_plan_s *p, int step, int G, int g) {
     if (!p) return fail(MDFFT_E_ARG, "null plan");
     if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan cannot execute");
     if (p->bd.kind != pl::kRowwise) return fail(MDFFT_E_ARG, "the distributed data plane is for row-wise plans");
@@ -170,7 +222,6 @@ mdfft_status check_dist(const mdfft_plan_s *p, int step, int G, int g, bool exch
     if (step < 0 || step >= p->M) return fail(MDFFT_E_ARG, "step out of range");
     if (G < 1 || G > p->P) return fail(MDFFT_E_ARG, "G must be in [1, P]");
     if (g < 0 || g >= G) return fail(MDFFT_E_ARG, "device index out of range");
-    (void)exchange;
     return MDFFT_OK;
 }
 
@@ -217,13 +268,16 @@ mdfft_status run_copy(mdfft_plan_s *p, int step, int G, int me, bool pack, const
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sms * 16);
+    // contiguous ranges of whole 256-point rounds, about 8 resident waves of CTAs
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 1023) / 1024, (int64_t)sms * 64));
+    const int64_t per_cta = ((total + blocks - 1) / blocks + 255) / 256 * 256;
+    const int small32 = total < (int64_t(1) << 32) ? 1 : 0;  // every box holds fewer than 2^32 points
     if (p->dt == MDFFT_C128)
         mdfft::dist::box_copy_kernel<double2><<<(unsigned)blocks, 256, 0, st>>>(
-            static_cast<const double2 *>(src), static_cast<double2 *>(dst), boxes, n, p->M, total);
+            static_cast<const double2 *>(src), static_cast<double2 *>(dst), boxes, n, p->M, total, per_cta, small32);
     else
         mdfft::dist::box_copy_kernel<float2><<<(unsigned)blocks, 256, 0, st>>>(
-            static_cast<const float2 *>(src), static_cast<float2 *>(dst), boxes, n, p->M, total);
+            static_cast<const float2 *>(src), static_cast<float2 *>(dst), boxes, n, p->M, total, per_cta, small32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, pack ? "pack launch" : "unpack launch");
     return MDFFT_OK;
@@ -243,7 +297,7 @@ mdfft_status mdfft_dist_local_range(mdfft_plan_t p, int step, int G, int g, int6
 
 mdfft_status mdfft_dist_lines(mdfft_plan_t p, int step, int G, int g, const void *in_local, void *out_local,
                               int dir, int normalize, mdfft_stream_t stream) {
-    mdfft_status cs = check_dist(p, step, G, g, false);
+    mdfft_status cs = check_dist(p, step, G, g);
     if (cs != MDFFT_OK) return cs;
     if (!in_local || !out_local) return fail(MDFFT_E_ARG, "null data pointer");
     if (dir != -1 && dir != 1) return fail(MDFFT_E_ARG, "dir must be -1 (forward) or +1 (inverse)");
@@ -296,14 +350,14 @@ mdfft_status mdfft_dist_lines(mdfft_plan_t p, int step, int G, int g, const void
 
 mdfft_status mdfft_dist_pack(mdfft_plan_t p, int step, int G, int g, const void *local, void *sendbuf,
                              mdfft_stream_t stream) {
-    mdfft_status cs = check_dist(p, step, G, g, true);
+    mdfft_status cs = check_dist(p, step, G, g);
     if (cs != MDFFT_OK) return cs;
     return run_copy(p, step, G, g, true, local, sendbuf, reinterpret_cast<cudaStream_t>(stream));
 }
 
 mdfft_status mdfft_dist_unpack(mdfft_plan_t p, int step, int G, int h, const void *recvbuf, void *local,
                                mdfft_stream_t stream) {
-    mdfft_status cs = check_dist(p, step, G, h, true);
+    mdfft_status cs = check_dist(p, step, G, h);
     if (cs != MDFFT_OK) return cs;
     return run_copy(p, step, G, h, false, recvbuf, local, reinterpret_cast<cudaStream_t>(stream));
 }
