@@ -62,3 +62,18 @@ def test_error_status_carries_the_message():
         md.Plan((8, 8, 7), 4)  # 7 is not a built line length
     assert e.value.status == md.mdfft.MDFFT_E_UNSUPPORTED
     assert "line length 7" in str(e.value)
+
+
+def test_fp64_rate_probe_measures_a_plausible_rate():
+    # the complex128 roofline's denominator: a positive multiply-add rate well
+    # below the FP32 class (GB300's FP64 rate is a small fraction of it)
+    out = torch.empty(152 * 256, dtype=torch.float64, device=DEV)
+    st = torch.cuda.current_stream(DEV).cuda_stream
+    tf = md.mdfft_fp64_rate_probe(out.data_ptr(), 152, 256, st)
+    assert 0.05 < tf < 20.0, tf
+    assert torch.isfinite(out).all()
+    with pytest.raises(md.MdfftError) as e:
+        md.mdfft_fp64_rate_probe(out.data_ptr(), 0, 256, st)
+    assert e.value.status == -1
+    with pytest.raises(md.MdfftError):
+        md.mdfft_fp64_rate_probe(0, 1, 1, st)
