@@ -64,6 +64,7 @@ def test_every_tuning_variant_gives_the_default_bits(shape, P, dt):
     x = torch.from_numpy(si.uniform_complex(shape, 970, np.complex64)).to(DEV)
     with md.Plan(shape, P, None, dt) as pl:
         want = pl.exec(x)
+        want_counts = pl.exec_counted(x)[1].cpu().tolist()
         base = pl.tuning()
         pl_default_radix = [d["radix"] for d in pl.describe()]
         tried = 0
@@ -82,6 +83,8 @@ def test_every_tuning_variant_gives_the_default_bits(shape, P, dt):
                     assert d["tile_order"] == order
                     tried += 1
                     y = pl.exec(x)
+                    # every variant's count mode counts the same moved and split-line points
+                    assert pl.exec_counted(x)[1].cpu().tolist() == want_counts, (v, s, d)
                     if "radix_alt" in v:  # another radix split: the same spectrum up to rounding
                         assert d["radix"] != pl_default_radix[s]
                         assert rel_l2(y, want) <= 1e-6, (v, s, d)
