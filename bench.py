@@ -43,7 +43,8 @@ PROFILE = os.path.join(ROOT, "profiles", "fft_pass_256cubed_c64.md")
 # everything the complex64 pass kernel is compiled from: its source, every
 # header it includes, and the build script that holds the nvcc flags
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1302_6189_gb300", "csrc", f) for f in
-                  ("fft_pass.cuh", "pass_c64.cu", "smem_layout.h", "tc_stage.cuh", "ptx_sync.cuh", "passes.h")] + \
+                  ("fft_pass.cuh", "pass_c64.cu", "smem_layout.h", "tc_stage.cuh", "ptx_sync.cuh", "passes.h",
+                   "fft_ring.cuh", "pass_ring.cu")] + \
                  [os.path.join(ROOT, "paper_1302_6189_gb300", "build.py")]
 
 

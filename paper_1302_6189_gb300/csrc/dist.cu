@@ -322,6 +322,7 @@ mdfft_status mdfft_dist_lines(mdfft_plan_t p, int step, int G, int g, const void
     const int64_t lines = (x1 - x0) / n;
     int Bg = std::max(1, std::min<int>(ps.k.lines, (int)std::min<int64_t>(lines, 1 << 20)));
     args.Bg = Bg, args.Bh = 1, args.Ng = lines, args.Nh = 1;
+    args.fd_bg = mdfft::fastdiv_make((uint32_t)Bg);
     args.gblocks = (lines + Bg - 1) / Bg;
     args.hblocks = 1;
     args.in_sg = n, args.out_sg = n, args.out_sf = 1;

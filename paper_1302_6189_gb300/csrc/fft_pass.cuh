@@ -84,6 +84,7 @@ struct PassArgs {
     int64_t ntiles;                 // tiles of the pass (persistent kernels walk them)
     int tile32;                     // every tile index and tile count fits 32 bits (cheaper divisions)
     FastDiv fd_g, fd_h, fd_rest[kMaxTileDims];  // gblocks, hblocks, rest_count as multiply-shift divisors
+    FastDiv fd_bg;                  // Bg as a multiply-shift divisor (tile line -> g, h; used when fd_bg.d == Bg)
     int *err;                       // persistent kernels: set to 1 if a bounded wait gave up (may be null)
     unsigned long long *moved;      // count mode: points whose owner changes (null: off)
     unsigned long long *split;      // count mode: split-line amount of the input layout
@@ -339,7 +340,8 @@ template <int R, typename C> __device__ __forceinline__ void dft(C (&v)[R]) {
 }
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-template <int G> __device__ __forceinline__ int padg(int i) { return i + i / G; }
+// (indices are never negative: unsigned division by the constant G is a shift)
+template <int G> __device__ __forceinline__ int padg(int i) { return i + (int)((unsigned)i / (unsigned)G); }
 
 }  // namespace mdfft
 
@@ -369,7 +371,11 @@ __device__ __forceinline__ int64_t owner_of(const OwnerMap &m, int64_t x) {
 // does DFT_R and writes y[(j / NS) NS R + j mod NS + r NS].
 // SRC selects where the first stage reads: -1 the default of the
 // configuration (HBM directly when DIRECT, else the staged tile), 2 a landing
-// buffer in shared memory holding the tile's lines unpadded (gsrc = the line).
+// buffer in shared memory holding the tile's lines unpadded (gsrc = the line),
+// 3 a slot of a ring of such buffers that is refilled only after the tile's
+// closing barrier (line-local stages keep their warp barriers); with 3 the
+// last stage writes a transposed-tile buffer of its own (tile != buf) that
+// nothing reads while the stages run, so it needs no barrier before its writes.
 template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC = -1, int RP = 0> struct Stages {
     using Cfg = PassCfg<Real, N, TC, THR, RP>;
     static constexpr int SRC0 = SRC >= 0 ? SRC : (Cfg::DIRECT ? 1 : 0);
@@ -441,7 +447,7 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
                         C x = __ldg(gsrc + j + r * NB);
                         if (conj) x.y = -x.y;
                         v[i][r] = x;
-                    } else if constexpr (FIRST && SRC0 == 2) {
+                    } else if constexpr (FIRST && (SRC0 == 2 || SRC0 == 3)) {
                         C x = gsrc[j + r * NB];
                         if (conj) x.y = -x.y;
                         v[i][r] = x;
@@ -453,7 +459,7 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
                 }
             }
         }
-        if constexpr (!(FIRST && SRC0 != 0)) {  // all reads of buf before any write
+        if constexpr (!(FIRST && SRC0 != 0) && !(LAST && SRC == 3)) {  // all reads of buf before any write
             if constexpr (WARP_LOCAL && !LAST) __syncwarp();
             else __syncthreads();
         }
@@ -461,13 +467,13 @@ template <typename Real, int N, int SI, int NS, int TC = 0, int THR = 0, int SRC
         for (int i = 0; i < PER; ++i) {
             const int j = t + i * Cfg::TL;
             if ((NB % Cfg::TL == 0 || j < NB) && ok) {
-                const int k = j % NS;
+                const int k = (int)((unsigned)j % (unsigned)NS);  // j >= 0: unsigned arithmetic by constants
                 if constexpr (NS > 1) {
 #pragma unroll
                     for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], tw[TWOFF + r * NS + k]);
                 }
                 dft<R>(v[i]);
-                const int base = (j / NS) * NS * R + k;
+                const int base = (int)((unsigned)j / (unsigned)NS) * NS * R + k;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if constexpr (LAST) {
@@ -496,6 +502,18 @@ struct TileCoord {
 // divisions run in 32 bits, several times cheaper than in 64.
 __device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv &f) {
     return (uint32_t)(((uint64_t)__umulhi(n, f.m) + n) >> f.l);
+}
+
+// Line l of a tile (g fastest) -> its position (bg, bh) along g and h: by the
+// multiply-shift divisor when the host set it for this Bg, else by division.
+__device__ __forceinline__ void tile_line(const PassArgs &a, int l, int &bg, int &bh) {
+    if (a.fd_bg.d == (uint32_t)a.Bg) {
+        bh = (int)fastdiv((uint32_t)l, a.fd_bg);
+        bg = l - bh * a.Bg;
+    } else {
+        bg = l % a.Bg;
+        bh = l / a.Bg;
+    }
 }
 
 __device__ __forceinline__ TileCoord tile_coords32(const PassArgs &a, uint32_t t) {
@@ -551,7 +569,8 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
     C *out = reinterpret_cast<C *>(a.out);
     const bool active = tid < Cfg::THREADS;
     const int sl = tid % Cfg::LINES, k0 = tid / Cfg::LINES;
-    const int sbg = sl % a.Bg, sbh = sl / a.Bg;
+    int sbg, sbh;
+    tile_line(a, sl, sbg, sbh);
     const bool sok = active && sl < a.Bg * a.Bh && c.g0 + sbg < a.Ng && c.h0 + sbh < a.Nh;
     unsigned long long moved = 0, split = 0;
     if (a.line_store) {  // the output keeps f fastest: every line is stored whole, k fastest across lanes
@@ -559,7 +578,8 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
         const Real sc = plain ? (Real)1 : (Real)a.scale, sy = (a.conj & 2) ? -sc : sc;
         for (int e = tid; e < Cfg::LINES * N && active; e += Cfg::THREADS) {
             const int l = e / N, k = e % N;
-            const int bg = l % a.Bg, bh = l / a.Bg;
+            int bg, bh;
+            tile_line(a, l, bg, bh);
             if (l < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
                 const int64_t o = c.out_base + bh * a.out_sh + bg * a.out_sg + k;
                 const C v = buf[k * Cfg::TROW + l];
@@ -579,8 +599,13 @@ __device__ __forceinline__ void store_tile(const PassArgs &a, const typename Pas
         const int64_t ostep = (int64_t)Cfg::TL * a.out_sf;
         const C *bp = buf + k0 * Cfg::TROW + sl;
         if (!(a.conj & 2) && !a.scaled) {  // all passes but the last of an inverse
+            if constexpr (N % Cfg::TL == 0) {  // N / TL elements per thread: a loop of fixed trip count
+#pragma unroll
+                for (int i = 0; i < N / Cfg::TL; ++i, op += ostep) *op = bp[i * Cfg::TL * Cfg::TROW];
+            } else {
 #pragma unroll 4
-            for (int k = k0; k < N; k += Cfg::TL, op += ostep, bp += Cfg::TL * Cfg::TROW) *op = *bp;
+                for (int k = k0; k < N; k += Cfg::TL, op += ostep, bp += Cfg::TL * Cfg::TROW) *op = *bp;
+            }
         } else {
             const Real sc = (Real)a.scale, sy = (a.conj & 2) ? -sc : sc;
 #pragma unroll 4
@@ -634,7 +659,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
         const TileCoord w0 = tile_coords(a, t);
         if (tid == 0) *shc = w0;
         for (int l = tid; l < Cfg::LINES; l += 32) {
-            const int bg = l % a.Bg, bh = l / a.Bg;
+            int bg, bh;
+            tile_line(a, l, bg, bh);
             lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
         }
     }
@@ -645,14 +671,16 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, int64_t t, unsigned
 
     // FFT role: thread (line, t) with t fastest
     const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
-    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    int fbg, fbh;
+    tile_line(a, line, fbg, fbh);
     const bool fok = active && line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh;
 
     if constexpr (!Cfg::DIRECT) {  // stage the whole tile through shared memory
         if (active) {
             for (int e = tid; e < Cfg::LINES * N; e += Cfg::THREADS) {
                 const int l = e / N, i = e % N;
-                const int bg = l % a.Bg, bh = l / a.Bg;
+                int bg, bh;
+                tile_line(a, l, bg, bh);
                 if (l < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
                     C x = in[lbase[l] + i];
                     if (a.conj & 1) x.y = -x.y;

@@ -47,7 +47,8 @@ __device__ __forceinline__ void pipe_issue(const PassArgs &a, int64_t t, float2 
     __syncwarp();
     const float2 *in = reinterpret_cast<const float2 *>(a.in);
     for (int l = lane; l < LINES; l += 32) {
-        const int bg = l % a.Bg, bh = l / a.Bg;
+        int bg, bh;
+        tile_line(a, l, bg, bh);
         if (l < a.Bg * a.Bh && bg < vg && bh < vh)
             bulk_copy_g2s(land + (size_t)l * N, in + c.in_base + bg * a.in_sg + bh * a.in_sh,
                           (uint32_t)(N * sizeof(float2)), bar);
@@ -86,14 +87,16 @@ __global__ void __launch_bounds__(PassCfg<float, N, 0, 0>::THREADS) fft_pass_pip
                 pipe_issue<N>(a, blockIdx.x + b * G, land + (size_t)b * P::LAND, &bar[b], lane);
 
     const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
-    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    int fbg, fbh;
+    tile_line(a, line, fbg, fbh);
     int64_t k = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += G, ++k) {
         const int b = (int)(k % NBUF);
         const uint32_t parity = (uint32_t)((k / NBUF) & 1);
         const TileCoord c = tile_coords(a, t);
         if (tid < Cfg::LINES) {
-            const int bg = tid % a.Bg, bh = tid / a.Bg;
+            int bg, bh;
+            tile_line(a, tid, bg, bh);
             lbase[tid] = c.in_base + bg * a.in_sg + bh * a.in_sh;
         }
         const bool ok = mbar_wait_bounded(&bar[b], parity, P::kWaitLimitNs);

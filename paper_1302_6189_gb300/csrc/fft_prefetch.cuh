@@ -31,7 +31,8 @@ template <int N, int RP = 0> struct PfCfg {
 template <int N, int RP>
 __device__ __forceinline__ bool pf_line(const PassArgs &a, int64_t t, int line, int64_t *base) {
     const TileCoord c = tile_coords(a, t);
-    const int bg = line % a.Bg, bh = line / a.Bg;
+    int bg, bh;
+    tile_line(a, line, bg, bh);
     *base = c.in_base + bg * a.in_sg + bh * a.in_sh;
     return line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
 }
@@ -93,7 +94,8 @@ __global__ void __launch_bounds__(PassCfg<float, N, 0, 0, RP>::THREADS, MINB) ff
             const TileCoord w0 = tile_coords(a, t);
             if (tid == 0) *shc = w0;
             for (int l = tid; l < Cfg::LINES; l += 32) {
-                const int bg = l % a.Bg, bh = l / a.Bg;
+                int bg, bh;
+                tile_line(a, l, bg, bh);
                 lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
             }
         }
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(PassCfg<float, 256>::THREADS, 4) fft_pass_shfl
         const TileCoord w0 = tile_coords(a, blockIdx.x);
         if (tid == 0) *shc = w0;
         for (int l = tid; l < Cfg::LINES; l += 32) {
-            const int bg = l % a.Bg, bh = l / a.Bg;
+            int bg, bh;
+            tile_line(a, l, bg, bh);
             lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
         }
     }
@@ -165,7 +168,8 @@ __global__ void __launch_bounds__(PassCfg<float, 256>::THREADS, 4) fft_pass_shfl
     __syncthreads();
     const TileCoord c = *shc;
     const int line = tid / 16, j = tid % 16;
-    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    int fbg, fbh;
+    tile_line(a, line, fbg, fbh);
     const bool ok = line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh;
     C v[16];
     const C *src = in + lbase[line];

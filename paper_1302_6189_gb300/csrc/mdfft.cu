@@ -59,6 +59,7 @@ void layout_strides(const pl::Layout &L, const int64_t *N, int64_t *stride) {
 
 // tile32 and the multiply-shift divisors of the tile decomposition (after any change of the tiling)
 void set_tile_divisors(PassArgs &a, int64_t ctas) {
+    a.fd_bg = mdfft::fastdiv_make((uint32_t)a.Bg);
     a.tile32 = ctas <= 0xffffffffLL;
     if (!a.tile32) return;
     a.fd_g = mdfft::fastdiv_make((uint32_t)a.gblocks);
@@ -309,6 +310,7 @@ int64_t mdfft::detail::wave_ctas(const PassKernel &k) {
         const int by_thr = thr_sm / k.threads;
         per = std::max(per, std::min(by_smem, std::min(by_regs, by_thr)));
     }
+    if (k.per_sm > 0) per = std::min(per, k.per_sm);
     return (int64_t)sms * std::max(per, 1);
 }
 
@@ -955,6 +957,24 @@ mdfft_status mdfft_exec_host(mdfft_plan_t p, const void *in_host, void *out_host
     return MDFFT_OK;
 }
 
+namespace {
+
+// The ring-of-slots kernels the autotuner tries (slots, resident CTAs per SM,
+// radix plan): two or three slots at two to four CTAs per SM, where two to
+// four tiles' loads in flight per SM measured best for 24-point lines; the
+// alternative radix plan only when the plan asks for radix search.
+struct RingVariant {
+    int slots, per_sm, rp;
+};
+constexpr RingVariant kRing[] = {{2, 3, 0}, {3, 2, 0}, {2, 4, 0}, {2, 2, 0}, {2, 3, 1}, {3, 2, 1}};
+constexpr int kRingVariants = (int)(sizeof(kRing) / sizeof(kRing[0]));
+bool ring_variant(int64_t n, int rv, bool tune_radix, PassKernel *k) {
+    if (rv < 0 || rv >= kRingVariants || (kRing[rv].rp && !tune_radix)) return false;
+    return mdfft::find_pass_kernel_ring(n, kRing[rv].slots, kRing[rv].per_sm, kRing[rv].rp, k);
+}
+
+}  // namespace
+
 mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int reps, mdfft_stream_t stream,
                                  float *ms_before, float *ms_after) {
     if (!p || !in || !out) return fail(MDFFT_E_ARG, "null argument");
@@ -975,10 +995,11 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
         if (p->dt == MDFFT_C64) {
             for (int thr : {256, 512, 192, 384})
                 if (mdfft::find_pass_kernel_c64_thr(ps.n, thr, &k) && k.threads != ps.k.threads) variants.push_back(k);
+            const bool al16 = (uintptr_t)in % 16 == 0 && (uintptr_t)out % 16 == 0;
             for (int nbuf : {1, 2})
-                if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && (uintptr_t)in % 16 == 0 &&
-                    (uintptr_t)out % 16 == 0)
-                    variants.push_back(k);
+                if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && al16) variants.push_back(k);
+            for (int rv = 0; rv < kRingVariants; ++rv)
+                if (ring_variant(ps.n, rv, (p->flags & MDFFT_PLAN_TUNE_RADIX) != 0, &k) && al16) variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_shfl(ps.n, &k)) variants.push_back(k);
@@ -1077,10 +1098,13 @@ namespace {
 // groups, with landing buffers / with first-stage loads from HBM, 12 / 13 the
 // persistent kernel with the next tile's loads in registers (2 / 4 CTAs per
 // SM), 14 / 15 the same with the alternative radix plan, 16 the 256-point
-// kernel with a warp-shuffle exchange between its two stages.
-constexpr int kTuningVariants = 17;
+// kernel with a warp-shuffle exchange between its two stages, 17-22 the
+// ring-of-slots kernel (kRing[variant - 17]: slots, CTAs per SM, radix plan).
+constexpr int kTuningVariants = 17 + kRingVariants;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
+    if (variant >= 17 && variant < kTuningVariants)
+        return p->dt == MDFFT_C64 && ring_variant(n, variant - 17, true, k);
     switch (variant) {
         case 16:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_shfl(n, k);
@@ -1130,7 +1154,7 @@ mdfft_status mdfft_plan_tuning(mdfft_plan_t p, int32_t *out, int cap) {
         int variant = -1;
         for (int v = 0; v < kTuningVariants && variant < 0; ++v) {
             PassKernel k;
-            if (tuning_kernel(p, s, v, &k) && k.fn == ps.k.fn) variant = v;
+            if (tuning_kernel(p, s, v, &k) && k.fn == ps.k.fn && k.per_sm == ps.k.per_sm) variant = v;
         }
         if (variant < 0) return fail(MDFFT_E_CUDA, "internal: unknown pass kernel");
         out[4 * s] = variant, out[4 * s + 1] = ps.args.Bg, out[4 * s + 2] = ps.args.Bh, out[4 * s + 3] = ps.mapping;

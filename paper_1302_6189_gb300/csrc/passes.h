@@ -22,6 +22,9 @@
 // buffers of a tile fit in shared memory).
 #define MDFFT_PIPE_LENGTHS(X) X(16) X(32) X(48) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
 
+// Line lengths with a persistent ring-of-slots variant (fft_ring.cuh).
+#define MDFFT_RING_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256)
+
 // Line lengths with fixed-CTA-size variants for the autotuner.
 #define MDFFT_TUNED_LENGTHS(X) X(32) X(48) X(64) X(96) X(128) X(160) X(192) X(256) X(512)
 
@@ -34,6 +37,7 @@ struct PassKernel {
     RadixPlan plan;      // radix plan of the kernel; its twiddle table follows tw_offset()
     int persistent = 0;  // > 0: walks tiles with a grid stride (launch at most one wave)
     int bulk = 0;        // 1: loads lines with bulk copies (input and output 16-byte aligned)
+    int per_sm = 0;      // persistent kernels: at most this many resident CTAs per SM (0: as many as fit)
 };
 
 bool find_pass_kernel_c64(int64_t n, PassKernel *k);
@@ -47,6 +51,7 @@ bool find_pass_kernel_c64_alt(int64_t n, PassKernel *k);           // alternativ
 bool find_pass_kernel_c64_occ(int64_t n, PassKernel *k);           // register cap for 6 CTAs per SM (24..64)
 bool find_pass_kernel_c64_pf(int64_t n, int rp, int minb, PassKernel *k);  // persistent, next tile's loads in registers
 bool find_pass_kernel_c64_shfl(int64_t n, PassKernel *k);          // 256: warp-shuffle exchange between the stages
+bool find_pass_kernel_ring(int64_t n, int slots, int per_sm, int rp, PassKernel *k);  // persistent, ring of slots
 bool find_move_kernel_c64(int64_t n, PassKernel *k);               // data movement of a pass, no FFT
 
 }  // namespace mdfft

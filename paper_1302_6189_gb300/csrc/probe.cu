@@ -23,12 +23,14 @@ __global__ void __launch_bounds__(PassCfg<float, N, 0, 0>::THREADS) move_pass_ke
     const C *in = reinterpret_cast<const C *>(a.in);
     const TileCoord c = tile_coords(a, blockIdx.x);
     if (tid < Cfg::LINES) {
-        const int bg = tid % a.Bg, bh = tid / a.Bg;
+        int bg, bh;
+        tile_line(a, tid, bg, bh);
         lbase[tid] = c.in_base + bg * a.in_sg + bh * a.in_sh;
     }
     __syncthreads();
     const int line = tid / Cfg::TL, tl = tid % Cfg::TL;
-    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    int fbg, fbh;
+    tile_line(a, line, fbg, fbh);
     if (line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh) {
         const C *src = in + lbase[line];
         C v[PER];

@@ -258,7 +258,8 @@ __device__ __forceinline__ void tcg_store(const PassArgs &a, const float2 *stage
     if (a.line_store) {
         for (int e = gt; e < K::LPG * N; e += 128) {
             const int l = e / N, k = e % N;
-            const int bg = l % a.Bg, bh = l / a.Bg;
+            int bg, bh;
+            tile_line(a, l, bg, bh);
             if (l < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
                 const int64_t o = c.out_base + bh * a.out_sh + bg * a.out_sg + k;
                 const float2 v = stage[l * K::PADN + pad16(k)];
@@ -274,7 +275,8 @@ __device__ __forceinline__ void tcg_store(const PassArgs &a, const float2 *stage
         }
     } else {
         const int sl = gt % K::LPG, k0 = gt / K::LPG;
-        const int bg = sl % a.Bg, bh = sl / a.Bg;
+        int bg, bh;
+        tile_line(a, sl, bg, bh);
         if (sl < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh) {
             const int64_t obase = c.out_base + bh * a.out_sh + bg * a.out_sg;
             float2 *op = out + obase + (int64_t)k0 * a.out_sf;
@@ -367,7 +369,8 @@ __global__ void __launch_bounds__(TcgCfg<N, TC, LAND_BUF>::THREADS, TcgCfg<N, TC
     for (; t < a.ntiles; t += stride, lpar ^= 1) {
         const TileCoord c = tile_coords(a, t);
         if (gt < K::LPG) {
-            const int bg = gt % a.Bg, bh = gt / a.Bg;
+            int bg, bh;
+            tile_line(a, gt, bg, bh);
             lbase[gt] = c.in_base + bg * a.in_sg + bh * a.in_sh;
         }
         if constexpr (LAND_BUF) {
@@ -376,7 +379,8 @@ __global__ void __launch_bounds__(TcgCfg<N, TC, LAND_BUF>::THREADS, TcgCfg<N, TC
             pending = false;
             bad = bad || !landed;
         }
-        const int fbg = line % a.Bg, fbh = line / a.Bg;
+        int fbg, fbh;
+        tile_line(a, line, fbg, fbh);
         const bool fok = line < a.Bg * a.Bh && c.g0 + fbg < a.Ng && c.h0 + fbh < a.Nh;
         const float2 *src = LAND_BUF ? land + line * N
                                      : reinterpret_cast<const float2 *>(a.in) + c.in_base + fbg * a.in_sg + fbh * a.in_sh;

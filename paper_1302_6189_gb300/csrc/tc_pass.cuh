@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(PassCfg<float, N, TC, THR>::THREADS, TcPassCfg
     if (tid < 32 && (int64_t)blockIdx.x < a.ntiles) pipe_issue<N, Cfg::LINES>(a, blockIdx.x, land, lbar, lane);
 
     const int line = tid / Cfg::TL, tl = tid % Cfg::TL;  // line < LINES: THREADS = TL x LINES
-    const int fbg = line % a.Bg, fbh = line / a.Bg;
+    int fbg, fbh;
+    tile_line(a, line, fbg, fbh);
     uint32_t par = 0, lpar = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += G, lpar ^= 1) {
         int64_t *lbase = coords + lpar * P::COORDS;  // input offset of each tile line
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(PassCfg<float, N, TC, THR>::THREADS, TcPassCfg
             const TileCoord w0 = tile_coords(a, t);
             if (tid == 0) *shc = w0;
             for (int l = tid; l < Cfg::LINES; l += 32) {
-                const int bg = l % a.Bg, bh = l / a.Bg;
+                int bg, bh;
+                tile_line(a, l, bg, bh);
                 lbase[l] = w0.in_base + bg * a.in_sg + bh * a.in_sh;
             }
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(lbar, lpar, kTcWaitNs))) {
