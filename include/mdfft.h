@@ -307,7 +307,8 @@ typedef struct {
     int64_t ctas;      /* tiles */
     int fft_axis, store_axis;  /* store_axis: the tile axis g */
     int64_t grid;      /* CTAs launched (= ctas unless persistent) */
-    int persistent;    /* 0: one CTA per tile; 1 or 2: persistent kernel with that many landing buffers */
+    int persistent;    /* 0: one CTA per tile; 1 to 3: persistent kernel with that many landing buffers
+                          (ring slots for variants 17-22 of mdfft_plan_tuning) */
     int stages;        /* radix stages of the line length's plan */
     int radix[12];     /* their radices, first stage first (e.g. 16, 16 for 256) */
     int tile_order;    /* 0: g is the output layout's fastest axis (runs of tile_g elements stored);
@@ -324,8 +325,11 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * several tile shapes (lines along the output's fastest axis x lines along
  * the next axis), `reps` launches each, and keeps the fastest.  For even
  * complex64 lengths up to 512 the candidates include a persistent kernel
- * that streams tiles through shared memory with bulk (TMA) copies; a plan
- * using it needs 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).
+ * that streams tiles through shared memory with bulk (TMA) copies, and for
+ * lengths 16, 24, 32, 48, 64, 96, 128 and 256 one that streams them through
+ * a ring of two or three shared-memory slots filled by 16-byte asynchronous
+ * copies, at a capped number of CTAs per SM; a plan using either needs
+ * 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).
  * Tensor-core plans (lengths 128, 256, 512) also try 128-thread CTAs (half
  * the lines per tile, more CTAs per SM) and, for 256 and 512, CTAs of two
  * independent 128-thread groups, and non-persistent kernels the
@@ -353,7 +357,10 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * the current tile runs (lengths 24, 32, 48, 64; registers for 2 / 4 CTAs
  * per SM), 14 / 15 the same with the alternative radix plan (64), 16 the
  * 256-point kernel that exchanges values between its two radix-16 stages
- * with warp shuffles instead of shared memory;
+ * with warp shuffles instead of shared memory, 17 / 18 / 19 / 20 the
+ * persistent ring-of-slots kernel with 2 / 3 / 2 / 2 slots at most 3 / 2 / 4
+ * / 2 CTAs per SM (lengths 16, 24, 32, 48, 64, 96, 128, 256), 21 / 22 the
+ * same as 17 / 18 with the alternative radix plan (64);
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,
