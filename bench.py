@@ -44,7 +44,7 @@ PROFILE = os.path.join(ROOT, "profiles", "fft_pass_256cubed_c64.md")
 # header it includes, and the build script that holds the nvcc flags
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1302_6189_gb300", "csrc", f) for f in
                   ("fft_pass.cuh", "pass_c64.cu", "smem_layout.h", "tc_stage.cuh", "ptx_sync.cuh", "passes.h",
-                   "fft_ring.cuh", "pass_ring.cu")] + \
+                   "fft_ring.cuh", "pass_ring.cu", "fft_line.cuh", "pass_line.cu")] + \
                  [os.path.join(ROOT, "paper_1302_6189_gb300", "build.py")]
 
 
@@ -803,10 +803,13 @@ def md_study(dev, reps=10):
             for want in (0, 1):
                 order, amount = mdfft_order_search(shape, P, want)
                 with Plan(shape, P, order, "c64", MDFFT_PLAN_TUNE_RADIX, batch=B) as pl:
-                    # the bound the passes' access pattern sets: the same loads and
-                    # transposed stores without the butterflies (default tiles)
-                    pattern_ms = [pl.pattern_probe(s_, x, y, reps=5) for s_ in range(M)]
                     pl.autotune(x, y, reps=3)
+                    # the bound the passes' access pattern sets: the same loads and
+                    # transposed stores without the butterflies (the chosen tiles)
+                    pattern_ms = [pl.pattern_probe(s_, x, y, reps=5) for s_ in range(M)]
+                    # and the same movement with S - 1 tiles' loads in flight per CTA
+                    # (persistent CTAs streaming tiles through a ring of slots)
+                    movement_ms = [movement_bound_ms(pl, s_, x, y) for s_ in range(M)]
                     tuning = [dict(t, radix=d["radix"]) for t, d in zip(pl.tuning(), pl.describe())]
                     for _ in range(3):
                         pl.exec(x, y)
@@ -824,6 +827,8 @@ def md_study(dev, reps=10):
                              "gbs": round(2 * M * T * 8 * B / (ms * 1e-3) / 1e9, 1),
                              "pass_ms": [round(v, 4) for v in pass_ms], "tuning": tuning,
                              "pattern_bound_gbs": [round(2 * B * T * 8 / (v * 1e-3) / 1e9, 1) for v in pattern_ms],
+                             "movement_bound_gbs": [round(2 * B * T * 8 / (v * 1e-3) / 1e9, 1) if v else None
+                                                    for v in movement_ms],
                              "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name))}
     return out
 
@@ -831,6 +836,20 @@ def md_study(dev, reps=10):
 # ncu summaries of the 4-D / 5-D configurations' launches (4 volumes, autotuned plan)
 MD_PROFILES = {"64x64x64x64 P=64 best": os.path.join(ROOT, "profiles", "fft_pass_64x4_c64.md"),
                "24x24x24x24x24 P=64 best": os.path.join(ROOT, "profiles", "fft_pass_24x5_c64.md")}
+
+
+def movement_bound_ms(pl, s, x, y):
+    """The fastest ring-structured data movement of pass s (mdfft_movement_probe:
+    2 slots at 3 CTAs per SM, 3 slots at 2), or None where no ring probe is built."""
+    from paper_1302_6189_gb300 import MdfftError
+    best = None
+    for slots, per_sm in ((2, 3), (3, 2)):
+        try:
+            ms = pl.movement_probe(s, x, y, slots, per_sm, reps=5)
+        except MdfftError:
+            return None
+        best = ms if best is None else min(best, ms)
+    return best
 
 
 def pass_roofline(launch_bytes, pass_ms, profile=None, volumes=1):
@@ -927,8 +946,8 @@ def precision_study(dev, with_oracle=True):
         xin = x.to(torch.complex128) if dt == "c128" else x
         y = torch.empty_like(xin)
         with Plan(shape, 4096, order, dt) as pl:
-            pattern_ms = [pl.pattern_probe(s_, xin, y, reps=3) for s_ in range(3)] if dt == "c64" else None
             pl.autotune(xin, y, reps=3)
+            pattern_ms = [pl.pattern_probe(s_, xin, y, reps=3) for s_ in range(3)] if dt == "c64" else None
             tuning = pl.tuning()
             for _ in range(2):
                 pl.exec(xin, y)

@@ -328,8 +328,10 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * that streams tiles through shared memory with bulk (TMA) copies, and for
  * lengths 16, 24, 32, 48, 64, 96, 128 and 256 one that streams them through
  * a ring of two or three shared-memory slots filled by 16-byte asynchronous
- * copies, at a capped number of CTAs per SM; a plan using either needs
- * 16-byte aligned arrays in mdfft_exec (E_ARG otherwise).
+ * copies, at a capped number of CTAs per SM, and for even lengths up to 64
+ * a kernel with one thread per line that keeps the line in registers through
+ * every radix stage; a plan using any of them needs 16-byte aligned arrays
+ * in mdfft_exec (E_ARG otherwise).
  * Tensor-core plans (lengths 128, 256, 512) also try 128-thread CTAs (half
  * the lines per tile, more CTAs per SM) and, for 256 and 512, CTAs of two
  * independent 128-thread groups, and non-persistent kernels the
@@ -360,7 +362,9 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * with warp shuffles instead of shared memory, 17 / 18 / 19 / 20 the
  * persistent ring-of-slots kernel with 2 / 3 / 2 / 2 slots at most 3 / 2 / 4
  * / 2 CTAs per SM (lengths 16, 24, 32, 48, 64, 96, 128, 256), 21 / 22 the
- * same as 17 / 18 with the alternative radix plan (64);
+ * same as 17 / 18 with the alternative radix plan (64), 23 one thread per
+ * line with every radix stage in registers (lengths 8, 12, 16, 20, 24, 30,
+ * 32, 40, 48, 60, 64; 16-byte aligned arrays);
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,
@@ -377,9 +381,10 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *ou
 
 /*
  * mdfft_pattern_probe -- runs `reps` times, on `stream`, a kernel that moves
- * the data of pass s exactly like the plan's default pass kernel (same tiles,
- * same loads, the same transposed stores into the next layout) but does no
- * butterflies, and returns its mean duration in ms.  Its bandwidth is the
+ * the data of pass s exactly like the plan's default pass kernel (the pass's
+ * tiles as built or autotuned when they fit the default CTA, else the
+ * default tiling; same loads, the same transposed stores into the next
+ * layout) but does no butterflies, and returns its mean duration in ms.  Its bandwidth is the
  * bound the redistribution's access pattern puts on the pass.  complex64
  * plans and line lengths 24, 32, 48, 64, 96, 128, 160, 192, 256, 512 only
  * (E_UNSUPPORTED otherwise).  in_dev is read, out_dev overwritten (T
@@ -387,6 +392,20 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t plan, const void *in_dev, void *ou
  */
 mdfft_status mdfft_pattern_probe(mdfft_plan_t plan, int s, const void *in_dev, void *out_dev, int reps,
                                  mdfft_stream_t stream, float *ms);
+
+/*
+ * mdfft_movement_probe -- the same data movement (out_dev receives what
+ * mdfft_pattern_probe writes) by a persistent kernel that streams the tiles
+ * through `slots` (2 or 3) shared-memory slots filled by 16-byte asynchronous
+ * copies, at most `per_sm` (1-8) CTAs per SM (tiles chosen as in
+ * mdfft_pattern_probe): the structure of the ring-of-slots pass kernel
+ * without its butterflies, so S - 1 tiles' loads stay in flight per CTA.  Its bandwidth bounds a pass kernel that hides the
+ * load latency that far.  complex64 plans, line lengths 16, 24, 32, 48, 64,
+ * 96, 128, 256, in_dev and out_dev 16-byte aligned (E_ARG / E_UNSUPPORTED
+ * otherwise); mean duration of `reps` launches in *ms; synchronises the stream.
+ */
+mdfft_status mdfft_movement_probe(mdfft_plan_t plan, int s, int slots, int per_sm, const void *in_dev, void *out_dev,
+                                  int reps, mdfft_stream_t stream, float *ms);
 
 /*
  * mdfft_fp64_rate_probe -- measures the device's FP64 multiply-add rate, the

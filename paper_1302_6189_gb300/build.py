@@ -23,7 +23,7 @@ LIB = os.path.join(LIBDIR, "libmdfft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I" + os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
-SOURCES = ["mdfft.cu", "planner.cpp", "pass_c64.cu", "pass_c128.cu", "pass_tc.cu", "serve.cu", "pass_c64_tuned.cu", "pass_pipe.cu", "probe.cu", "pass_c64_alt.cu", "dist.cu", "pass_ring.cu"]
+SOURCES = ["mdfft.cu", "planner.cpp", "pass_c64.cu", "pass_c128.cu", "pass_tc.cu", "serve.cu", "pass_c64_tuned.cu", "pass_pipe.cu", "probe.cu", "pass_c64_alt.cu", "dist.cu", "pass_ring.cu", "pass_line.cu"]
 
 
 def _nvcc():

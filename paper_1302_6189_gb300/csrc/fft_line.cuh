@@ -1,0 +1,146 @@
+// fft_line.cuh -- complex64 pass kernel for short lines with one thread per
+// line: the thread holds its line in registers and runs every radix stage of
+// the default kernel's plan there, so no shared memory and no barrier lies
+// between the stages, and it stores its outputs straight from registers.
+//
+// The same pass as fft_pass_kernel (the Fig. 4 step and the transpose after
+// it): the same radix plan, twiddles and butterflies in the same order, so
+// the results are bit-identical.  What changes is the work per point.  With
+// several threads per line (the default shape of lengths up to 64) every
+// thread repeats its stage's addressing, predicates and loop control for a
+// few points, a radix that does not divide the line's butterflies among the
+// threads leaves lanes idle, and the stages exchange values through shared
+// memory behind barriers; here each instruction of a warp does the work of
+// 32 lines.
+//
+// A warp owns 32 consecutive lines of the tile.  It copies them (16-byte
+// units, consecutive lanes on consecutive units of a line) into its own
+// staging rows in shared memory; after __syncwarp each lane reads its row
+// (16-byte reads: the row stride, 2 mod 4 elements, puts 8 consecutive rows
+// on distinct bank groups), transforms it and writes element k of its line
+// for k = 0 .. N-1: at fixed k the lanes write consecutive points of the
+// tile's g axis, the output layout's fastest (runs of Bg elements, as the
+// default store writes).  No CTA barrier at all: the twiddles come from the
+// read-only cache (the same table the default kernel stages).
+#pragma once
+
+#include "fft_pass.cuh"
+
+namespace mdfft {
+
+// the radix stages of PassCfg<float, N>'s plan on a line held in registers:
+// stage SI after NS points already combined, butterfly j as in Stages::simt
+template <int N, int SI, int NS> struct RegStages {
+    static constexpr RadixPlan P = PassCfg<float, N>::plan;
+    static constexpr int R = P.R[SI], NB = N / R, TWOFF = tw_offset(P, SI);
+    __device__ __forceinline__ static void run(float2 (&x)[N], const float2 *tw) {
+        float2 y[N];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = x[j + r * NB];
+            const int k = j % NS;
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + TWOFF + r * NS + k));
+            }
+            dft<R>(v);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) y[base + r * NS] = v[r];
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = y[i];
+        if constexpr (SI + 1 < P.S) RegStages<N, SI + 1, NS * R>::run(x, tw);
+    }
+};
+
+template <int N> struct LineCfg {
+    static_assert(N % 2 == 0 && N >= 2, "lines are copied in 16-byte units (two complex64)");
+    static constexpr RadixPlan plan = PassCfg<float, N>::plan;
+    static constexpr int WARPS = 4, LINES = 32 * WARPS, THREADS = LINES;
+    static constexpr int CH = N / 2;                     // 16-byte units per line
+    static constexpr int RS = N % 4 == 2 ? N : N + 2;    // staging row stride (complex64), 2 mod 4
+    static constexpr size_t SMEM = (size_t)LINES * RS * sizeof(float2) + (size_t)LINES * sizeof(int64_t);
+};
+
+template <int N>
+__global__ void __launch_bounds__(LineCfg<N>::THREADS) fft_pass_line_kernel(const PassArgs a) {
+    using LC = LineCfg<N>;
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char line_smem[];
+    C *stage = reinterpret_cast<C *>(line_smem);                        // [LINES][RS]
+    int64_t *lbase = reinterpret_cast<int64_t *>(stage + LC::LINES * LC::RS);  // input offset of each line, -1: none
+    const int tid = threadIdx.x, lane = tid & 31, w0 = tid - lane;
+    const C *in = reinterpret_cast<const C *>(a.in);
+    C *out = reinterpret_cast<C *>(a.out);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+
+    const TileCoord c = tile_coords(a, blockIdx.x);
+    int bg, bh;
+    tile_line(a, tid, bg, bh);
+    const bool ok = tid < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
+    const int64_t ib = c.in_base + (int64_t)bg * a.in_sg + (int64_t)bh * a.in_sh;
+    lbase[tid] = ok ? ib : -1;
+    __syncwarp();
+    // the warp's 32 lines into its rows: unit e = lane + 32 i is unit u of line l
+#pragma unroll
+    for (int i = 0; i < LC::CH; ++i) {
+        const int e = lane + 32 * i, l = e / LC::CH, u = e - l * LC::CH;
+        const int64_t b = lbase[w0 + l];
+        if (b >= 0) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(stage + (w0 + l) * LC::RS + 2 * u);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(in + b + 2 * u) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+
+    C x[N];
+    const C *row = stage + tid * LC::RS;
+#pragma unroll
+    for (int u = 0; u < LC::CH; ++u) {
+        const float4 q = *reinterpret_cast<const float4 *>(row + 2 * u);
+        x[2 * u] = C{q.x, q.y};
+        x[2 * u + 1] = C{q.z, q.w};
+    }
+    if (a.conj & 1)
+#pragma unroll
+        for (int k = 0; k < N; ++k) x[k].y = -x[k].y;
+    if constexpr (LC::plan.S > 0) RegStages<N, 0, 1>::run(x, gtw);
+
+    const int64_t ob = c.out_base + (int64_t)bh * a.out_sh + (int64_t)bg * a.out_sg;
+    if (ok) {
+        C *op = out + ob;
+        if (!(a.conj & 2) && !a.scaled) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) op[k * a.out_sf] = x[k];
+        } else {
+            const float sc = (float)a.scale, sy = (a.conj & 2) ? -sc : sc;
+#pragma unroll
+            for (int k = 0; k < N; ++k) op[k * a.out_sf] = C{x[k].x * sc, x[k].y * sy};
+        }
+    }
+    if (a.moved) {  // count mode: owner of every point before and after, the split-line amount once per line
+        unsigned long long moved = 0, split = 0;
+        if (ok) {
+            for (int k = 0; k < N; ++k)
+                moved += owner_of(a.own_in, ib + k) != owner_of(a.own_out, ob + k * a.out_sf);
+            split = (unsigned long long)N *
+                    ((owner_of(a.own_in, ib + N - 1) - owner_of(a.own_in, ib)) / a.own_in.line_div);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            moved += __shfl_down_sync(0xffffffffu, moved, o);
+            split += __shfl_down_sync(0xffffffffu, split, o);
+        }
+        if (lane == 0) {
+            if (moved) atomicAdd(a.moved, moved);
+            if (split) atomicAdd(a.split, split);
+        }
+    }
+}
+
+}  // namespace mdfft

@@ -241,8 +241,18 @@ template <typename Real, int N, int TC = 0, int THR = 0, int RP = 0> struct Pass
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+// Sums of two products with the contraction written out: one rounded
+// product and one fused multiply-add, the same in every kernel that inlines
+// them (left to the compiler, either product may be the fused one, and
+// kernels that compute the same butterflies could round differently).
+__device__ __forceinline__ float fma_prod(float a, float b, float c, float d) {
+    return __fmaf_rn(a, b, __fmul_rn(c, d));  // a b + c d
+}
+__device__ __forceinline__ double fma_prod(double a, double b, double c, double d) {
+    return __fma_rn(a, b, __dmul_rn(c, d));
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+    return {fma_prod(a.x, b.x, -a.y, b.y), fma_prod(a.x, b.y, a.y, b.x)};
 }
 
 // w_16^k = cos(2 pi k/16) - i sin(2 pi k/16), k < 8: cosines and sines of
@@ -324,8 +334,8 @@ template <typename C> __device__ __forceinline__ void dft5(C (&v)[5]) {
     C x0 = v[0];
     C p1 = {x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y};
     C p2 = {x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y};
-    C q1 = {s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y};  // X1 = p1 - i q1, X4 = p1 + i q1
-    C q2 = {s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y};  // X2 = p2 - i q2, X3 = p2 + i q2
+    C q1 = {fma_prod(s1, b1.x, s2, b2.x), fma_prod(s1, b1.y, s2, b2.y)};    // X1 = p1 - i q1, X4 = p1 + i q1
+    C q2 = {fma_prod(s2, b1.x, -s1, b2.x), fma_prod(s2, b1.y, -s1, b2.y)};  // X2 = p2 - i q2, X3 = p2 + i q2
     v[0] = {x0.x + a1.x + a2.x, x0.y + a1.y + a2.y};
     v[1] = {p1.x + q1.y, p1.y - q1.x};
     v[4] = {p1.x - q1.y, p1.y + q1.x};

@@ -1000,6 +1000,7 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && al16) variants.push_back(k);
             for (int rv = 0; rv < kRingVariants; ++rv)
                 if (ring_variant(ps.n, rv, (p->flags & MDFFT_PLAN_TUNE_RADIX) != 0, &k) && al16) variants.push_back(k);
+            if (mdfft::find_pass_kernel_line(ps.n, &k) && al16) variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_shfl(ps.n, &k)) variants.push_back(k);
@@ -1099,12 +1100,14 @@ namespace {
 // persistent kernel with the next tile's loads in registers (2 / 4 CTAs per
 // SM), 14 / 15 the same with the alternative radix plan, 16 the 256-point
 // kernel with a warp-shuffle exchange between its two stages, 17-22 the
-// ring-of-slots kernel (kRing[variant - 17]: slots, CTAs per SM, radix plan).
-constexpr int kTuningVariants = 17 + kRingVariants;
+// ring-of-slots kernel (kRing[variant - 17]: slots, CTAs per SM, radix plan),
+// 23 one thread per line with the stages in registers.
+constexpr int kLineVariant = 17 + kRingVariants;
+constexpr int kTuningVariants = kLineVariant + 1;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
-    if (variant >= 17 && variant < kTuningVariants)
-        return p->dt == MDFFT_C64 && ring_variant(n, variant - 17, true, k);
+    if (variant >= 17 && variant < kLineVariant) return p->dt == MDFFT_C64 && ring_variant(n, variant - 17, true, k);
+    if (variant == kLineVariant) return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_line(n, k);
     switch (variant) {
         case 16:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_shfl(n, k);
@@ -1211,6 +1214,21 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t p, int s, mdfft_pass_info *out) {
     return MDFFT_OK;
 }
 
+namespace {
+// The tiling a probe of pass s moves: the pass's own tiles (as built or
+// autotuned) when they fit a CTA of `lines` lines, else the default tiling.
+void probe_tiling(const mdfft_plan_s *p, int s, int lines, PassArgs *a, int64_t *ctas) {
+    const Pass &ps = p->pass[s];
+    if ((int64_t)ps.args.Bg * ps.args.Bh <= lines) {
+        *a = ps.args;
+        *ctas = ps.ctas;
+        set_tile_divisors(*a, ps.ctas);
+    } else {
+        mdfft::detail::retile_pass(p, s, lines, a, ctas);
+    }
+}
+}  // namespace
+
 mdfft_status mdfft_pattern_probe(mdfft_plan_t p, int s, const void *in, void *out, int reps, mdfft_stream_t stream,
                                  float *ms) {
     if (!p || !in || !out || !ms) return fail(MDFFT_E_ARG, "null argument");
@@ -1221,9 +1239,9 @@ mdfft_status mdfft_pattern_probe(mdfft_plan_t p, int s, const void *in, void *ou
     if (ps.args.line_store) return fail(MDFFT_E_UNSUPPORTED, "the pass stores whole lines: no transpose to probe");
     PassKernel k;
     if (!mdfft::find_move_kernel_c64(ps.n, &k)) return fail(MDFFT_E_UNSUPPORTED, "no probe for this line length");
-    PassArgs a;  // the default tiling of this length
+    PassArgs a;
     int64_t ctas = 0;
-    mdfft::detail::retile_pass(p, s, k.lines, &a, &ctas);
+    probe_tiling(p, s, k.lines, &a, &ctas);
     a.in = in, a.out = out, a.scale = 1.0, a.scaled = 0, a.conj = 0, a.moved = nullptr, a.split = nullptr;
     if (k.smem > 48 * 1024 &&
         cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
@@ -1237,6 +1255,46 @@ mdfft_status mdfft_pattern_probe(mdfft_plan_t p, int s, const void *in, void *ou
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
         e = cudaLaunchKernel(k.fn, dim3((unsigned)ctas), dim3(k.threads), args, k.smem, st);
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+    *ms = t / (float)reps;
+    return MDFFT_OK;
+}
+
+mdfft_status mdfft_movement_probe(mdfft_plan_t p, int s, int slots, int per_sm, const void *in, void *out, int reps,
+                                  mdfft_stream_t stream, float *ms) {
+    if (!p || !in || !out || !ms) return fail(MDFFT_E_ARG, "null argument");
+    if (p->flags & MDFFT_PLAN_HOST_ONLY) return fail(MDFFT_E_ARG, "host-only plan");
+    if (s < 0 || s >= p->M || reps < 1) return fail(MDFFT_E_ARG, "bad pass index or reps");
+    if (per_sm < 1 || per_sm > 8) return fail(MDFFT_E_ARG, "per_sm must be in [1, 8]");
+    if ((uintptr_t)in % 16 || (uintptr_t)out % 16) return fail(MDFFT_E_ARG, "in and out must be 16-byte aligned");
+    if (p->dt != MDFFT_C64) return fail(MDFFT_E_UNSUPPORTED, "complex64 plans only");
+    const Pass &ps = p->pass[s];
+    if (ps.args.line_store) return fail(MDFFT_E_UNSUPPORTED, "the pass stores whole lines: no transpose to probe");
+    PassKernel k;
+    if (!mdfft::find_move_ring_kernel_c64(ps.n, slots, &k))
+        return fail(MDFFT_E_UNSUPPORTED, "no ring probe for this line length or slot count");
+    k.per_sm = per_sm;
+    PassArgs a;
+    int64_t ctas = 0;
+    probe_tiling(p, s, k.lines, &a, &ctas);
+    a.in = in, a.out = out, a.scale = 1.0, a.scaled = 0, a.conj = 0, a.moved = nullptr, a.split = nullptr;
+    a.ntiles = ctas;
+    const int64_t grid = std::min<int64_t>(ctas, mdfft::detail::wave_ctas(k));  // sets the shared-memory limit
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(k.threads), args, k.smem, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(k.threads), args, k.smem, st);
     cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float t = 0.f;

@@ -25,6 +25,9 @@
 // Line lengths with a persistent ring-of-slots variant (fft_ring.cuh).
 #define MDFFT_RING_LENGTHS(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256)
 
+// Even line lengths with a one-thread-per-line variant (fft_line.cuh).
+#define MDFFT_LINE_LENGTHS(X) X(8) X(12) X(16) X(20) X(24) X(30) X(32) X(40) X(48) X(60) X(64)
+
 // Line lengths with fixed-CTA-size variants for the autotuner.
 #define MDFFT_TUNED_LENGTHS(X) X(32) X(48) X(64) X(96) X(128) X(160) X(192) X(256) X(512)
 
@@ -52,6 +55,8 @@ bool find_pass_kernel_c64_occ(int64_t n, PassKernel *k);           // register c
 bool find_pass_kernel_c64_pf(int64_t n, int rp, int minb, PassKernel *k);  // persistent, next tile's loads in registers
 bool find_pass_kernel_c64_shfl(int64_t n, PassKernel *k);          // 256: warp-shuffle exchange between the stages
 bool find_pass_kernel_ring(int64_t n, int slots, int per_sm, int rp, PassKernel *k);  // persistent, ring of slots
+bool find_pass_kernel_line(int64_t n, PassKernel *k);              // one thread per line, stages in registers
 bool find_move_kernel_c64(int64_t n, PassKernel *k);               // data movement of a pass, no FFT
+bool find_move_ring_kernel_c64(int64_t n, int slots, PassKernel *k);  // the same through a ring of slots
 
 }  // namespace mdfft

@@ -83,6 +83,8 @@ SIGNATURES = {
     "mdfft_workspace_size": (c_int, [c_void_p, P_(c_size_t)]),
     "mdfft_plan_check": (c_int, [c_void_p]),
     "mdfft_pattern_probe": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p, P_(ctypes.c_float)]),
+    "mdfft_movement_probe": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p,
+                                     P_(ctypes.c_float)]),
     "mdfft_launches_per_exec": (c_int, [c_void_p, P_(c_int)]),
     "mdfft_fp64_rate_probe": (c_int, [c_void_p, c_int, i64, c_void_p, P_(ctypes.c_double)]),
     "mdfft_dist_local_range": (c_int, [c_void_p, c_int, c_int, c_int, P_(i64), P_(i64)]),
@@ -198,7 +200,7 @@ def mdfft_selftest_wait(arrive, limit_us):
 
 TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384", "radix_alt", "occ6", "tcg", "tcg_direct", "pf2", "pf4",
                    "pf2_radix_alt", "pf4_radix_alt", "shfl256", "ring2x3", "ring3x2", "ring2x4", "ring2x2",
-                   "ring2x3_radix_alt", "ring3x2_radix_alt")
+                   "ring2x3_radix_alt", "ring3x2_radix_alt", "line")
 
 
 def mdfft_plan_tuning(plan, M):
@@ -306,6 +308,13 @@ def mdfft_plan_autotune(plan, in_ptr, out_ptr, reps, stream, M):
     _check(_lib.mdfft_plan_autotune(plan, c_void_p(in_ptr), c_void_p(out_ptr), int(reps), c_void_p(stream),
                                     before, after), "mdfft_plan_autotune")
     return list(before), list(after)
+
+
+def mdfft_movement_probe(plan, s, slots, per_sm, in_ptr, out_ptr, reps, stream):
+    ms = ctypes.c_float()
+    _check(_lib.mdfft_movement_probe(plan, int(s), int(slots), int(per_sm), c_void_p(in_ptr), c_void_p(out_ptr),
+                                     int(reps), c_void_p(stream), ctypes.byref(ms)), "mdfft_movement_probe")
+    return ms.value
 
 
 def mdfft_pattern_probe(plan, s, in_ptr, out_ptr, reps, stream):
@@ -570,6 +579,13 @@ class Plan:
         self._check_tensor(x, "input")
         self._check_tensor(scratch, "scratch", self.out_shape)
         return mdfft_pattern_probe(self.handle, s, x.data_ptr(), scratch.data_ptr(), reps, self._stream(stream))
+
+    def movement_probe(self, s, x, scratch, slots=2, per_sm=3, reps=10, stream=None):
+        """ms per launch of the same data movement through a ring of `slots` slots, `per_sm` CTAs per SM."""
+        self._check_tensor(x, "input")
+        self._check_tensor(scratch, "scratch", self.out_shape)
+        return mdfft_movement_probe(self.handle, s, slots, per_sm, x.data_ptr(), scratch.data_ptr(), reps,
+                                    self._stream(stream))
 
     def tuning(self):
         """The launch choices of every pass (store them, e.g. as JSON, after autotune)."""

@@ -356,6 +356,36 @@ def test_pattern_probe_moves_the_data_of_a_pass():
     assert np.array_equal(got, np.transpose(x.cpu().numpy(), (0, 2, 1)))
 
 
+@pytest.mark.parametrize("shape,P", [((64, 48, 32), 4), ((24, 20, 24, 24), 64), ((40, 64, 30), 16)])
+def test_movement_probe_moves_what_the_pattern_probe_moves(shape, P):
+    # the ring-structured probe (persistent CTAs, 2 or 3 slots, a CTA cap per
+    # SM) writes exactly the pattern probe's output, every pass it is built for
+    x = torch.from_numpy(si.uniform_complex(shape, 96, np.complex64)).to(DEV)
+    with md.Plan(shape, P, None, "c64") as plan:
+        probed = 0
+        for s in range(len(shape)):
+            want = torch.zeros_like(x)
+            try:
+                plan.pattern_probe(s, x, want, reps=1)
+            except md.MdfftError:
+                continue
+            for slots, per_sm in ((2, 3), (3, 2), (2, 1)):
+                got = torch.zeros_like(x)
+                try:
+                    ms = plan.movement_probe(s, x, got, slots, per_sm, reps=2)
+                except md.MdfftError as e:
+                    assert e.status == -7, e  # E_UNSUPPORTED: no ring build for this length
+                    break
+                assert ms > 0
+                assert torch.equal(got, want), (s, slots, per_sm)
+                probed += 1
+        assert probed >= 3
+        with pytest.raises(md.MdfftError):
+            plan.movement_probe(0, x, torch.empty_like(x), 4, 2)
+        with pytest.raises(md.MdfftError):
+            plan.movement_probe(0, x, torch.empty_like(x), 2, 0)
+
+
 @pytest.mark.parametrize("shape", [(4, 2, 3, 2, 4, 2), (2, 2, 3, 2, 2, 2, 5), (2, 3, 2, 2, 2, 2, 2, 4)])
 def test_six_to_eight_dims_with_the_heuristic_order(shape):
     x = si.uniform_complex(shape, 98)

@@ -1,7 +1,8 @@
 """The ring-of-slots pass kernel (a persistent CTA streaming its tiles
 through S shared-memory slots filled by 16-byte asynchronous copies, with a
-cap of resident CTAs per SM) computes exactly what the default pass kernel
-computes: the same stages and store, only the first stage reads a slot.
+cap of resident CTAs per SM) and the one-thread-per-line kernel (every radix
+stage on a line held in registers) compute exactly what the default pass
+kernel computes: the same radix plan and butterflies in the same order.
 Checked bit for bit on every length it is built for, on ragged tiles,
 batches, the per-volume host path, the normalised inverse and count mode;
 the spectrum is also checked against the oracle."""
@@ -16,7 +17,7 @@ import synth_inputs as si
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
-RING = [v for v in md.mdfft.TUNING_VARIANTS if v.startswith("ring")]
+RING = [v for v in md.mdfft.TUNING_VARIANTS if v.startswith("ring")] + ["line"]
 
 
 def ring_tuning(pl, variant, tile):
@@ -50,7 +51,7 @@ def test_ring_variants_give_the_default_bits(shape, P, batch):
         want_counts = pl.exec_counted(x)[1].cpu().tolist()
         tried, walks = 0, 0.0
         for v in RING:
-            for tile in ((8, 8), (5, 3), (16, 4)):
+            for tile in ((8, 8), (5, 3), (16, 4), (24, 5)):
                 chosen, hit = ring_tuning(pl, v, tile)
                 if not hit:
                     continue
@@ -62,6 +63,9 @@ def test_ring_variants_give_the_default_bits(shape, P, batch):
                 pl.set_tuning(chosen)
                 d = pl.describe()
                 for s in hit:
+                    if v == "line":
+                        assert d[s]["persistent"] == 0 and d[s]["threads"] == 128, (v, s, d[s])
+                        continue
                     assert d[s]["persistent"] in (2, 3) and d[s]["grid"] <= d[s]["ctas"], (v, s, d[s])
                     walks = max(walks, d[s]["ctas"] / d[s]["grid"])
                 tried += 1
@@ -94,3 +98,26 @@ def test_ring_24_cubed_four_dims_against_the_oracle():
     want = oracle.fftn(x, -1, nthreads=8)
     err = np.abs(got - want).max() / np.abs(want).max()
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("shape,P", [((24, 24, 24, 24), 64), ((16, 48, 32, 8), 16), ((64, 60, 40), 8)])
+def test_line_kernel_on_every_pass_against_the_oracle(shape, P):
+    # every pass whose length has the one-thread-per-line kernel runs it, with
+    # the default tiles; element-wise against the FP64 oracle, forward and
+    # normalised inverse
+    x = si.uniform_complex(shape, 996, np.complex64)
+    with md.Plan(shape, P, None, "c64") as pl:
+        base = pl.tuning()
+        chosen, hit = ring_tuning(pl, "line", (base[0]["tile_g"], base[0]["tile_h"]))
+        if not hit:
+            chosen, hit = ring_tuning(pl, "line", (8, 4))
+        assert hit
+        pl.set_tuning(chosen)
+        xd = torch.from_numpy(x).to(DEV)
+        got = pl.exec(xd)
+        back = pl.exec(got, dir=1, normalize=True).cpu().numpy()
+        got = got.cpu().numpy().astype(np.complex128)
+    want = oracle.fftn(x, -1, nthreads=8)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-5, err
+    assert np.abs(back - x).max() < 1e-5
