@@ -28,10 +28,11 @@
 
 namespace mdfft {
 
-// the radix stages of PassCfg<float, N>'s plan on a line held in registers:
-// stage SI after NS points already combined, butterfly j as in Stages::simt
-template <int N, int SI, int NS> struct RegStages {
-    static constexpr RadixPlan P = PassCfg<float, N>::plan;
+// the radix stages of PassCfg<float, N, 0, 0, RP>'s plan on a line held in
+// registers: stage SI after NS points already combined, butterfly j as in
+// Stages::simt
+template <int N, int SI, int NS, int RP = 0> struct RegStages {
+    static constexpr RadixPlan P = PassCfg<float, N, 0, 0, RP>::plan;
     static constexpr int R = P.R[SI], NB = N / R, TWOFF = tw_offset(P, SI);
     __device__ __forceinline__ static void run(float2 (&x)[N], const float2 *tw) {
         float2 y[N];
@@ -52,22 +53,23 @@ template <int N, int SI, int NS> struct RegStages {
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) x[i] = y[i];
-        if constexpr (SI + 1 < P.S) RegStages<N, SI + 1, NS * R>::run(x, tw);
+        if constexpr (SI + 1 < P.S) RegStages<N, SI + 1, NS * R, RP>::run(x, tw);
     }
 };
 
-template <int N> struct LineCfg {
+// RP: the radix plan (as in PassCfg); WARPS: warps per CTA (32 lines each)
+template <int N, int RP = 0, int WARPS = 4> struct LineCfg {
     static_assert(N % 2 == 0 && N >= 2, "lines are copied in 16-byte units (two complex64)");
-    static constexpr RadixPlan plan = PassCfg<float, N>::plan;
-    static constexpr int WARPS = 4, LINES = 32 * WARPS, THREADS = LINES;
+    static constexpr RadixPlan plan = PassCfg<float, N, 0, 0, RP>::plan;
+    static constexpr int LINES = 32 * WARPS, THREADS = LINES;
     static constexpr int CH = N / 2;                     // 16-byte units per line
     static constexpr int RS = N % 4 == 2 ? N : N + 2;    // staging row stride (complex64), 2 mod 4
     static constexpr size_t SMEM = (size_t)LINES * RS * sizeof(float2) + (size_t)LINES * sizeof(int64_t);
 };
 
-template <int N>
-__global__ void __launch_bounds__(LineCfg<N>::THREADS) fft_pass_line_kernel(const PassArgs a) {
-    using LC = LineCfg<N>;
+template <int N, int RP = 0, int WARPS = 4>
+__global__ void __launch_bounds__(LineCfg<N, RP, WARPS>::THREADS) fft_pass_line_kernel(const PassArgs a) {
+    using LC = LineCfg<N, RP, WARPS>;
     using C = float2;
     extern __shared__ __align__(16) unsigned char line_smem[];
     C *stage = reinterpret_cast<C *>(line_smem);                        // [LINES][RS]
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) fft_pass_line_kernel(cons
     if (a.conj & 1)
 #pragma unroll
         for (int k = 0; k < N; ++k) x[k].y = -x[k].y;
-    if constexpr (LC::plan.S > 0) RegStages<N, 0, 1>::run(x, gtw);
+    if constexpr (LC::plan.S > 0) RegStages<N, 0, 1, RP>::run(x, gtw);
 
     const int64_t ob = c.out_base + (int64_t)bh * a.out_sh + (int64_t)bg * a.out_sg;
     if (ok) {

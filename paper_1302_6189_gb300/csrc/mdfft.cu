@@ -973,6 +973,18 @@ bool ring_variant(int64_t n, int rv, bool tune_radix, PassKernel *k) {
     return mdfft::find_pass_kernel_ring(n, kRing[rv].slots, kRing[rv].per_sm, kRing[rv].rp, k);
 }
 
+// The one-thread-per-line kernels (radix plan, warps per CTA): 4 warps, 2
+// warps, and the alternative radix plan when the plan asks for radix search.
+struct LineVariant {
+    int rp, warps;
+};
+constexpr LineVariant kLine[] = {{0, 4}, {0, 2}, {1, 4}};
+constexpr int kLineVariants = (int)(sizeof(kLine) / sizeof(kLine[0]));
+bool line_variant(int64_t n, int lv, bool tune_radix, PassKernel *k) {
+    if (lv < 0 || lv >= kLineVariants || (kLine[lv].rp && !tune_radix)) return false;
+    return mdfft::find_pass_kernel_line(n, kLine[lv].rp, kLine[lv].warps, k);
+}
+
 }  // namespace
 
 mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int reps, mdfft_stream_t stream,
@@ -1000,7 +1012,8 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 if (mdfft::find_pass_kernel_pipe(ps.n, nbuf, &k) && al16) variants.push_back(k);
             for (int rv = 0; rv < kRingVariants; ++rv)
                 if (ring_variant(ps.n, rv, (p->flags & MDFFT_PLAN_TUNE_RADIX) != 0, &k) && al16) variants.push_back(k);
-            if (mdfft::find_pass_kernel_line(ps.n, &k) && al16) variants.push_back(k);
+            for (int lv = 0; lv < kLineVariants; ++lv)
+                if (line_variant(ps.n, lv, (p->flags & MDFFT_PLAN_TUNE_RADIX) != 0, &k) && al16) variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_shfl(ps.n, &k)) variants.push_back(k);
@@ -1101,13 +1114,14 @@ namespace {
 // SM), 14 / 15 the same with the alternative radix plan, 16 the 256-point
 // kernel with a warp-shuffle exchange between its two stages, 17-22 the
 // ring-of-slots kernel (kRing[variant - 17]: slots, CTAs per SM, radix plan),
-// 23 one thread per line with the stages in registers.
+// 23-25 one thread per line with the stages in registers (kLine[variant - 23]).
 constexpr int kLineVariant = 17 + kRingVariants;
-constexpr int kTuningVariants = kLineVariant + 1;
+constexpr int kTuningVariants = kLineVariant + kLineVariants;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     if (variant >= 17 && variant < kLineVariant) return p->dt == MDFFT_C64 && ring_variant(n, variant - 17, true, k);
-    if (variant == kLineVariant) return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_line(n, k);
+    if (variant >= kLineVariant && variant < kTuningVariants)
+        return p->dt == MDFFT_C64 && line_variant(n, variant - kLineVariant, true, k);
     switch (variant) {
         case 16:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_shfl(n, k);

@@ -5,18 +5,38 @@
 
 namespace mdfft {
 
-template <int N> static PassKernel make_line() {
-    using LC = LineCfg<N>;
-    PassKernel k{(const void *)&fft_pass_line_kernel<N>, LC::THREADS, LC::LINES, 1, LC::SMEM, LC::plan};
+template <int N, int RP, int WARPS> static PassKernel make_line() {
+    using LC = LineCfg<N, RP, WARPS>;
+    PassKernel k{(const void *)&fft_pass_line_kernel<N, RP, WARPS>, LC::THREADS, LC::LINES, 1, LC::SMEM, LC::plan};
     k.bulk = 1;  // 16-byte copies from line starts: input and output 16-byte aligned
     return k;
 }
 
-bool find_pass_kernel_line(int64_t n, PassKernel *k) {
+// rp 0: the default radix plan, 4 or 2 warps per CTA (2: the register-heavy
+// lengths 48 to 64, more CTAs per SM); rp 1: the alternative plan of 32 and
+// 64 (4 warps)
+bool find_pass_kernel_line(int64_t n, int rp, int warps, PassKernel *k) {
+    if (rp == 1) {
+        if (warps != 4) return false;
+        if (n == 32) *k = make_line<32, 1, 4>();
+        else if (n == 64) *k = make_line<64, 1, 4>();
+        else return false;
+        return true;
+    }
+    if (rp != 0) return false;
+    if (warps == 2) {
+        switch (n) {
+            case 48: *k = make_line<48, 0, 2>(); return true;
+            case 60: *k = make_line<60, 0, 2>(); return true;
+            case 64: *k = make_line<64, 0, 2>(); return true;
+            default: return false;
+        }
+    }
+    if (warps != 4) return false;
     switch (n) {
-#define MDFFT_CASE(N)         \
-    case N:                   \
-        *k = make_line<N>();  \
+#define MDFFT_CASE(N)                 \
+    case N:                           \
+        *k = make_line<N, 0, 4>();    \
         return true;
         MDFFT_LINE_LENGTHS(MDFFT_CASE)
 #undef MDFFT_CASE
