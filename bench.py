@@ -40,11 +40,11 @@ METRIC = "M-D FFT GB/s & % HBM peak vs plain; served FFT/s, p50/p99 at stated er
 SHAPE = (256, 256, 256)
 P_DEFAULT = 4096
 PROFILE = os.path.join(ROOT, "profiles", "fft_pass_256cubed_c64.md")
-# everything the complex64 pass kernel is compiled from: its source, every
-# header it includes, and the build script that holds the nvcc flags
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1302_6189_gb300", "csrc", f) for f in
-                  ("fft_pass.cuh", "pass_c64.cu", "smem_layout.h", "tc_stage.cuh", "ptx_sync.cuh", "passes.h",
-                   "fft_ring.cuh", "pass_ring.cu", "fft_line.cuh", "pass_line.cu")] + \
+# everything the profiled kernels are compiled from: every CUDA source and
+# header of the library (the autotuner may pick any variant), and the build
+# script that holds the nvcc flags
+_CSRC = os.path.join(ROOT, "paper_1302_6189_gb300", "csrc")
+KERNEL_SOURCES = sorted(os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".cu", ".cuh", ".h"))) + \
                  [os.path.join(ROOT, "paper_1302_6189_gb300", "build.py")]
 
 
