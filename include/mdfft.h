@@ -461,9 +461,12 @@ mdfft_status mdfft_destroy(mdfft_plan_t plan);
  * (those of mdfft_exec): a lone request then runs its passes back to back
  * instead of one per step.  Line lengths
  * 16, 24, 32, 48, 64, 96, 128, 160, 192, 256 run inside the persistent
- * kernel; other supported lengths run as separate launches in the same step.
- * Results are the same as mdfft_exec's for the same shape (same kernels and
- * tiles).  All work goes to `stream`; the caller's buffers must stay valid
+ * kernel; passes of 16 to 64 points whose arrays are 16-byte aligned go
+ * instead to a second persistent kernel of the same graph, launched after
+ * it, that runs one thread per line with every radix stage in registers
+ * (mdfft_server_set_line_kernel); other supported lengths run as separate
+ * launches in the same step.  Results are the same as mdfft_exec's for the
+ * same shape (the same radix plans and butterflies in the same order).  All work goes to `stream`; the caller's buffers must stay valid
  * until the request is done.  Errors: E_ARG, E_RANGE (request above the
  * whole budget), E_UNSUPPORTED, E_NOMEM, E_CUDA.
  */
@@ -528,6 +531,11 @@ mdfft_status mdfft_server_set_chunk(mdfft_server_t s, int chunk);
  * remaining passes directly, oldest request first.  Results do not depend on
  * it. */
 mdfft_status mdfft_server_set_direct(mdfft_server_t s, int max_requests);
+/* 1 (default): passes of 16 to 64 points with 16-byte aligned arrays run in
+ * the line kernel of the step; 0: in the grouped persistent kernel like the
+ * other lengths.  Takes effect at the next step; results do not depend on
+ * it.  E_ARG unless enable is 0 or 1. */
+mdfft_status mdfft_server_set_line_kernel(mdfft_server_t s, int enable);
 mdfft_status mdfft_server_get_stats(mdfft_server_t s, mdfft_server_stats *out);
 mdfft_status mdfft_server_destroy(mdfft_server_t s);
 

@@ -67,32 +67,32 @@ template <int N, int RP = 0, int WARPS = 4> struct LineCfg {
     static constexpr size_t SMEM = (size_t)LINES * RS * sizeof(float2) + (size_t)LINES * sizeof(int64_t);
 };
 
-template <int N, int RP = 0, int WARPS = 4>
-__global__ void __launch_bounds__(LineCfg<N, RP, WARPS>::THREADS) fft_pass_line_kernel(const PassArgs a) {
-    using LC = LineCfg<N, RP, WARPS>;
+// One warp's 32 lines of tile c: tile lines w0 .. w0 + 31, lane = line - w0.
+// stage: the warp's 32 staging rows (RS elements each), lbase: 32 entries.
+// Begins with __syncwarp, so a warp may run it for tile after tile.
+template <int N, int RP = 0>
+__device__ __forceinline__ void line_warp(const PassArgs &a, const TileCoord &c, int w0, float2 *stage,
+                                          int64_t *lbase, int lane) {
+    using LC = LineCfg<N, RP, 1>;
     using C = float2;
-    extern __shared__ __align__(16) unsigned char line_smem[];
-    C *stage = reinterpret_cast<C *>(line_smem);                        // [LINES][RS]
-    int64_t *lbase = reinterpret_cast<int64_t *>(stage + LC::LINES * LC::RS);  // input offset of each line, -1: none
-    const int tid = threadIdx.x, lane = tid & 31, w0 = tid - lane;
     const C *in = reinterpret_cast<const C *>(a.in);
     C *out = reinterpret_cast<C *>(a.out);
     const C *gtw = reinterpret_cast<const C *>(a.tw);
-
-    const TileCoord c = tile_coords(a, blockIdx.x);
+    const int line = w0 + lane;
     int bg, bh;
-    tile_line(a, tid, bg, bh);
-    const bool ok = tid < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
+    tile_line(a, line, bg, bh);
+    const bool ok = line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
     const int64_t ib = c.in_base + (int64_t)bg * a.in_sg + (int64_t)bh * a.in_sh;
-    lbase[tid] = ok ? ib : -1;
+    __syncwarp();  // the previous tile's reads of the rows and offsets are done
+    lbase[lane] = ok ? ib : -1;
     __syncwarp();
     // the warp's 32 lines into its rows: unit e = lane + 32 i is unit u of line l
 #pragma unroll
     for (int i = 0; i < LC::CH; ++i) {
         const int e = lane + 32 * i, l = e / LC::CH, u = e - l * LC::CH;
-        const int64_t b = lbase[w0 + l];
+        const int64_t b = lbase[l];
         if (b >= 0) {
-            const unsigned d = (unsigned)__cvta_generic_to_shared(stage + (w0 + l) * LC::RS + 2 * u);
+            const unsigned d = (unsigned)__cvta_generic_to_shared(stage + l * LC::RS + 2 * u);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(in + b + 2 * u) : "memory");
         }
     }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(LineCfg<N, RP, WARPS>::THREADS) fft_pass_line_
     __syncwarp();
 
     C x[N];
-    const C *row = stage + tid * LC::RS;
+    const C *row = stage + lane * LC::RS;
 #pragma unroll
     for (int u = 0; u < LC::CH; ++u) {
         const float4 q = *reinterpret_cast<const float4 *>(row + 2 * u);
@@ -143,6 +143,18 @@ __global__ void __launch_bounds__(LineCfg<N, RP, WARPS>::THREADS) fft_pass_line_
             if (split) atomicAdd(a.split, split);
         }
     }
+}
+
+// One tile of LINES = 32 WARPS lines per CTA; warp w takes tile lines 32 w ..
+template <int N, int RP = 0, int WARPS = 4>
+__global__ void __launch_bounds__(LineCfg<N, RP, WARPS>::THREADS) fft_pass_line_kernel(const PassArgs a) {
+    using LC = LineCfg<N, RP, WARPS>;
+    extern __shared__ __align__(16) unsigned char line_smem[];
+    float2 *stage = reinterpret_cast<float2 *>(line_smem);                     // [LINES][RS]
+    int64_t *lbase = reinterpret_cast<int64_t *>(stage + LC::LINES * LC::RS);  // input offset of each line, -1: none
+    const int tid = threadIdx.x, lane = tid & 31, w0 = tid - lane;
+    const TileCoord c = tile_coords(a, blockIdx.x);
+    line_warp<N, RP>(a, c, w0, stage + w0 * LC::RS, lbase + w0, lane);
 }
 
 }  // namespace mdfft

@@ -9,9 +9,12 @@
 // memory, then the persistent kernel), captured once per table slot.  The
 // persistent kernel walks the tiles of all items with a grid stride; a CTA
 // finds the item of a tile by binary search over the items' first tiles and
-// runs the tile code of that item's line length.  There is no device-side
-// waiting: passes of one request are in consecutive steps, ordered by the
-// stream.
+// runs the tile code of that item's line length.  Passes of lines of 16 to
+// 64 points (16-byte aligned arrays) go instead to a second persistent
+// kernel of the same graph, launched after the first, whose warps each take
+// whole 32-line tiles and run the one-thread-per-line code of fft_line.cuh.
+// There is no device-side waiting: passes of one request are in consecutive
+// steps, ordered by the stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +26,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "fft_line.cuh"
 #include "plan_internal.h"
 
 using mdfft::PassArgs;
@@ -52,11 +56,39 @@ struct Item {
 };
 
 struct Table {
-    int n;
+    int n;          // items of the grouped kernel: items[0, n)
     int chunk;      // consecutive tiles dealt to a CTA at a time
     int64_t total;  // tiles in the step
+    int n2;         // items of the line kernel: items[n, n + n2), tiles numbered from 0 among them
+    int chunk2;     // consecutive 32-line tiles dealt to a warp at a time
+    int64_t total2;
     Item items[kMaxItems];
 };
+
+// line lengths of the one-thread-per-line serving kernel: kind kLineKind + i
+#define MDFFT_SERVE_LINE_LENGTHS(X) X(0, 16) X(1, 24) X(2, 32) X(3, 48) X(4, 64)
+constexpr int kLineKind = 100;
+constexpr int kLineThreads = 128, kLineWarps = kLineThreads / 32;
+constexpr size_t kArgsBytes = (sizeof(PassArgs) + 15) / 16 * 16;
+constexpr size_t cmax2(size_t a, size_t b) { return a > b ? a : b; }
+#define MDFFT_LINE_RS_MAX(i, N) cmax2((size_t)LineCfg<N>::RS,
+#define MDFFT_LINE_CLOSE(i, N) )
+constexpr size_t kLineRs = MDFFT_SERVE_LINE_LENGTHS(MDFFT_LINE_RS_MAX) 0 MDFFT_SERVE_LINE_LENGTHS(MDFFT_LINE_CLOSE);
+// per warp: the item's arguments, 32 staging rows, 32 line offsets
+constexpr size_t kLineWarpSmem = kArgsBytes + 32 * kLineRs * sizeof(float2) + 32 * sizeof(int64_t);
+constexpr size_t kLineSmem = kLineWarps * kLineWarpSmem;
+
+int line_kind_of(int64_t n) {
+    switch (n) {
+#define MDFFT_KIND(i, N) \
+    case N:              \
+        return kLineKind + i;
+        MDFFT_SERVE_LINE_LENGTHS(MDFFT_KIND)
+#undef MDFFT_KIND
+        default:
+            return -1;
+    }
+}
 
 template <int N> using ServeCfg = PassCfg<float, N, 0, kThreads>;
 template <int N> constexpr size_t smem_of() { return ServeCfg<N>::SMEM; }
@@ -142,6 +174,57 @@ __global__ void __launch_bounds__(kThreads, 4) serve_kernel(const Table *tab) {
     }
 }
 
+// The line kernel: warp w of the grid takes chunks of chunk2 consecutive
+// 32-line tiles of the line items in turn; it copies an item's arguments to
+// its own shared memory when it reaches the item's tiles (items are in
+// increasing tile order, so lookups only advance).  No CTA barrier.
+__global__ void __launch_bounds__(kLineThreads, 2) serve_line_kernel(const Table *tab) {
+    extern __shared__ __align__(16) unsigned char line_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wsm = line_smem + warp * kLineWarpSmem;
+    PassArgs &args = *reinterpret_cast<PassArgs *>(wsm);
+    float2 *stage = reinterpret_cast<float2 *>(wsm + kArgsBytes);
+    int64_t *lbase = reinterpret_cast<int64_t *>(stage + 32 * kLineRs);
+    const Item *items = tab->items + tab->n;
+    const int n = tab->n2;
+    const int64_t total = tab->total2;
+    const int64_t chunk = tab->chunk2;
+    const int64_t gw = (int64_t)blockIdx.x * kLineWarps + warp, nw = (int64_t)gridDim.x * kLineWarps;
+    int cur = -1, kind = -1;
+    int64_t cur_start = 0, cur_end = 0;
+    for (int64_t c0 = gw * chunk; c0 < total; c0 += nw * chunk)
+        for (int64_t t = c0; t < c0 + chunk && t < total; ++t) {
+            if (t >= cur_end) {  // the last item after cur starting at or before t
+                int lo = cur + 1, hi = n - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (items[mid].start <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                cur = lo;
+                cur_start = items[cur].start;
+                cur_end = cur + 1 < n ? items[cur + 1].start : total;
+                __syncwarp();  // every lane is done with the previous arguments
+                const int *src = reinterpret_cast<const int *>(&items[cur].args);
+                int *dst = reinterpret_cast<int *>(&args);
+                for (int w = lane; w < (int)(sizeof(PassArgs) / sizeof(int)); w += 32) dst[w] = src[w];
+                kind = items[cur].kind;
+                __syncwarp();
+            }
+            const TileCoord c = tile_coords(args, t - cur_start);
+            switch (kind) {
+#define MDFFT_RUN(i, N)                                           \
+    case kLineKind + i:                                           \
+        line_warp<N>(args, c, 0, stage, lbase, lane);             \
+        break;
+                MDFFT_SERVE_LINE_LENGTHS(MDFFT_RUN)
+#undef MDFFT_RUN
+                default:
+                    break;
+            }
+        }
+}
+
 // first-fit allocator over one device arena (offsets 256-byte aligned)
 class Arena {
   public:
@@ -217,10 +300,13 @@ struct Slot {
 
 using namespace mdfft::serve;
 
-struct ServePass {  // a plan's pass re-tiled for the persistent kernel
-    PassArgs args;
+struct ServePass {  // a plan's pass re-tiled for the persistent kernels
+    PassArgs args;      // for the grouped kernel (kind >= 0)
     int64_t ctas;
     int kind;
+    PassArgs line_args;  // for the line kernel (line_kind >= 0): 32-line tiles
+    int64_t line_tiles;
+    int line_kind;
 };
 
 struct mdfft_server_s {
@@ -241,6 +327,10 @@ struct mdfft_server_s {
     int depth = 2;  // steps in flight on the GPU at most; arrivals in between join the next step
     int chunk = 4;  // at most this many consecutive tiles dealt to a CTA at a time
     int direct = 4;  // low load: at most this many requests with passes left run them as plain launches
+    int lines = 1;   // passes of 16 to 64 points go to the line kernel
+    int line_grid = 0;
+    cudaStream_t capture2 = nullptr;            // the line kernel's branch of the step graph
+    cudaEvent_t fork = nullptr, join = nullptr;  // the branch starts after the table copy, the step ends after both
     Slot slots[kSlots];
     int next_slot = 0;
     cudaEvent_t t0 = nullptr;
@@ -256,7 +346,14 @@ mdfft_status capture_graphs(mdfft_server_t s) {
         cudaError_t e = cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
         cudaMemcpyAsync(sl.dev, sl.host, sizeof(Table), cudaMemcpyHostToDevice, s->capture);
+        // the two kernels are parallel branches: the line kernel's CTAs take
+        // SMs as the grouped kernel's CTAs finish, and the other way round
+        cudaEventRecord(s->fork, s->capture);
+        cudaStreamWaitEvent(s->capture2, s->fork, 0);
         serve_kernel<<<s->grid, kThreads, kSmem, s->capture>>>(sl.dev);
+        serve_line_kernel<<<s->line_grid, kLineThreads, kLineSmem, s->capture2>>>(sl.dev);
+        cudaEventRecord(s->join, s->capture2);
+        cudaStreamWaitEvent(s->capture, s->join, 0);
         e = cudaStreamEndCapture(s->capture, &sl.graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
@@ -314,6 +411,9 @@ mdfft_status get_plan(mdfft_server_t s, int M, const int64_t *N, mdfft_plan_t *o
         rt[q].kind = kind_of(p->pass[q].n);
         rt[q].ctas = 0;
         if (rt[q].kind >= 0) mdfft::detail::retile_pass(p, q, lines_of_kind(rt[q].kind), &rt[q].args, &rt[q].ctas);
+        rt[q].line_kind = line_kind_of(p->pass[q].n);
+        rt[q].line_tiles = 0;
+        if (rt[q].line_kind >= 0) mdfft::detail::retile_pass(p, q, 32, &rt[q].line_args, &rt[q].line_tiles);
     }
     s->retiled[p] = rt;
     *out = p;
@@ -370,8 +470,12 @@ mdfft_status mdfft_server_create(mdfft_server_t *out, size_t budget_bytes, int m
     s->arena_bytes = (budget_bytes / 3 + 255) / 256 * 256;
     if ((e = cudaMalloc(&s->arena_mem, s->arena_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc arena"));
     s->arena.reset(s->arena_bytes);
-    if ((e = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&s->capture2, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaStreamCreate"));
+    if ((e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaEventCreate"));
     if ((e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
         cudaSuccess)
         return bail(cuda_fail(e, "cudaFuncSetAttribute"));
@@ -380,6 +484,12 @@ mdfft_status mdfft_server_create(mdfft_server_t *out, size_t budget_bytes, int m
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kThreads, kSmem);
     s->grid = std::max(1, sms * std::max(1, per_sm));
+    if ((e = cudaFuncSetAttribute(serve_line_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmem)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "cudaFuncSetAttribute"));
+    int line_per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&line_per_sm, serve_line_kernel, kLineThreads, kLineSmem);
+    s->line_grid = std::max(1, sms * std::max(1, line_per_sm));
     for (Slot &sl : s->slots) {
         if ((e = cudaHostAlloc((void **)&sl.host, sizeof(Table), cudaHostAllocDefault)) != cudaSuccess)
             return bail(cuda_fail(e, "cudaHostAlloc table"));
@@ -491,15 +601,27 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         return MDFFT_OK;
     }
     Table *tab = sl.host;
-    int n = 0;
-    int64_t total = 0;
-    std::vector<std::pair<Request *, PassArgs>> separate;  // lengths the persistent kernel does not carry
+    int n = 0, n2 = 0;
+    int64_t total = 0, total2 = 0;
+    std::vector<std::pair<Request *, PassArgs>> separate;  // lengths the persistent kernels do not carry
+    std::vector<Item> line_items;
     for (Request *r : todo) {
-        if (n >= kMaxItems) break;
+        if (n + n2 >= kMaxItems) break;
         const int pass = r->next_pass;
         const PassArgs a = pass_args(s, r, pass);
         const ServePass &sp = s->retiled[r->plan][pass];
-        if (sp.kind < 0) {
+        const bool al16 = (uintptr_t)a.in % 16 == 0 && (uintptr_t)a.out % 16 == 0;
+        if (s->lines && sp.line_kind >= 0 && al16) {  // the same pass in 32-line tiles for the line kernel
+            line_items.emplace_back();
+            Item &it = line_items.back();
+            it.args = sp.line_args;
+            it.args.in = a.in, it.args.out = a.out, it.args.tw = a.tw;
+            it.args.conj = a.conj, it.args.scale = a.scale, it.args.scaled = a.scaled;
+            it.start = total2;
+            it.kind = sp.line_kind;
+            total2 += sp.line_tiles;
+            n2++;
+        } else if (sp.kind < 0) {
             separate.push_back({r, a});
         } else {  // the same pass re-tiled for the persistent kernel's CTA
             Item &it = tab->items[n++];
@@ -521,9 +643,14 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     // the step's tiles spread over every CTA first: chunks of total / grid tiles, at most s->chunk
     tab->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(s->chunk, total / std::max(1, s->grid)));
     tab->total = total;
-    if (n > 0) {
+    for (int i = 0; i < n2; ++i) tab->items[n + i] = line_items[i];
+    tab->n2 = n2;
+    tab->chunk2 = (int)std::max<int64_t>(
+        1, std::min<int64_t>(s->chunk, total2 / std::max<int64_t>(1, (int64_t)s->line_grid * kLineWarps)));
+    tab->total2 = total2;
+    if (n + n2 > 0) {
         if (sl.copy) {  // copy only the header and the items of this step
-            const size_t used = offsetof(Table, items) + (size_t)n * sizeof(Item);
+            const size_t used = offsetof(Table, items) + (size_t)(n + n2) * sizeof(Item);
             e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy, sl.dev, sl.host, used, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphExecMemcpyNodeSetParams1D");
         }
@@ -660,6 +787,12 @@ mdfft_status mdfft_server_set_grid(mdfft_server_t s, int ctas) {
     return capture_graphs(s);
 }
 
+mdfft_status mdfft_server_set_line_kernel(mdfft_server_t s, int enable) {
+    if (!s || (enable != 0 && enable != 1)) return fail(MDFFT_E_ARG, "enable must be 0 or 1");
+    s->lines = enable;
+    return MDFFT_OK;
+}
+
 mdfft_status mdfft_server_set_chunk(mdfft_server_t s, int chunk) {
     if (!s || chunk < 1 || chunk > 64) return fail(MDFFT_E_ARG, "chunk must be in [1, 64]");
     s->chunk = chunk;
@@ -699,6 +832,9 @@ mdfft_status mdfft_server_destroy(mdfft_server_t s) {
     }
     if (s->t0) cudaEventDestroy(s->t0);
     if (s->capture) cudaStreamDestroy(s->capture);
+    if (s->capture2) cudaStreamDestroy(s->capture2);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
     if (s->arena_mem) cudaFree(s->arena_mem);
     for (auto &kv : s->plans) mdfft_destroy(kv.second);
     for (auto &kv : s->requests) delete kv.second;

@@ -108,6 +108,7 @@ SIGNATURES = {
     "mdfft_server_set_depth": (c_int, [c_void_p, c_int]),
     "mdfft_server_set_chunk": (c_int, [c_void_p, c_int]),
     "mdfft_server_set_direct": (c_int, [c_void_p, c_int]),
+    "mdfft_server_set_line_kernel": (c_int, [c_void_p, c_int]),
     "mdfft_server_get_stats": (c_int, [c_void_p, P_(MdfftServerStats)]),
     "mdfft_server_destroy": (c_int, [c_void_p]),
 }
@@ -454,6 +455,10 @@ def mdfft_server_set_direct(server, max_requests):
     _check(_lib.mdfft_server_set_direct(server, int(max_requests)), "mdfft_server_set_direct")
 
 
+def mdfft_server_set_line_kernel(server, enable):
+    _check(_lib.mdfft_server_set_line_kernel(server, int(enable)), "mdfft_server_set_line_kernel")
+
+
 def mdfft_server_get_stats(server):
     st = MdfftServerStats()
     _check(_lib.mdfft_server_get_stats(server, ctypes.byref(st)), "mdfft_server_get_stats")
@@ -673,6 +678,9 @@ class Server:
 
     def set_direct(self, max_requests):
         mdfft_server_set_direct(self.handle, max_requests)
+
+    def set_line_kernel(self, enable):
+        mdfft_server_set_line_kernel(self.handle, int(enable))
 
     def stats(self):
         return mdfft_server_get_stats(self.handle)

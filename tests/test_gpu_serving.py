@@ -230,3 +230,37 @@ def test_low_load_direct_launches_give_the_same_bits(direct):
             srv.set_direct(-1)
     for sh, x, y in zip(shapes, xs, outs):
         assert torch.equal(y, alone(sh, x, -1, False)), sh
+
+
+@pytest.mark.parametrize("line_kernel", [0, 1])
+def test_line_kernel_switch_and_8_byte_aligned_buffers(line_kernel):
+    # passes of 16 to 64 points go to the step's one-thread-per-line kernel
+    # when it is on and the request's arrays are 16-byte aligned, else to the
+    # grouped kernel: every result equals mdfft_exec's either way (requests 1
+    # and 3 use arrays that start 8 bytes past a 16-byte boundary)
+    shapes = [(32, 32, 32, 32), (48, 64, 24), (16, 64, 48), (24, 24, 24), (64, 96, 32)]
+    xs, outs = [], []
+    for i, sh in enumerate(shapes):
+        T = int(np.prod(sh))
+        data = torch.from_numpy(si.uniform_complex(sh, 1900 + i, np.complex64)).to(DEV)
+        if i in (1, 3):
+            xb = torch.empty(T + 1, dtype=torch.complex64, device=DEV)
+            ob = torch.empty(T + 1, dtype=torch.complex64, device=DEV)
+            x, y = xb[1:].view(sh), ob[1:].view(sh)
+            x.copy_(data)
+            assert x.data_ptr() % 16 == 8 and y.data_ptr() % 16 == 8
+        else:
+            x, y = data, torch.empty_like(data)
+        xs.append(x)
+        outs.append(y)
+    with md.Server(budget_bytes=1 << 30, max_inflight=8) as srv:
+        srv.set_direct(0)
+        srv.set_line_kernel(line_kernel)
+        for x, y in zip(xs, outs):
+            srv.submit(x, y)
+        srv.drain()
+        assert srv.stats()["completed"] == len(shapes)
+        with pytest.raises(md.MdfftError):
+            srv.set_line_kernel(2)
+    for sh, x, y in zip(shapes, xs, outs):
+        assert torch.equal(y, alone(sh, x.contiguous(), -1, False)), sh
