@@ -59,24 +59,34 @@ struct Table {
     int n;          // items of the grouped kernel: items[0, n)
     int chunk;      // consecutive tiles dealt to a CTA at a time
     int64_t total;  // tiles in the step
-    int n2;         // items of the line kernel: items[n, n + n2), tiles numbered from 0 among them
-    int chunk2;     // consecutive 32-line tiles dealt to a warp at a time
-    int64_t total2;
+    // items of the line kernels, group g after those of the groups before:
+    // items[n + n_line[0] + .. + n_line[g-1], + n_line[g]), tiles numbered from 0 in each group
+    int n_line[2];
+    int chunk_line[2];  // consecutive 32-line tiles dealt to a warp at a time
+    int64_t total_line[2];
     Item items[kMaxItems];
 };
 
-// line lengths of the one-thread-per-line serving kernel: kind kLineKind + i
+// line lengths of the one-thread-per-line serving kernels: kind kLineKind + i;
+// group 0 (16, 24, 32: up to 90 registers a thread in the standalone
+// kernel) and group 1 (48, 64: up to 190) are separate kernels, so that the
+// short lengths keep more warps per SM
 #define MDFFT_SERVE_LINE_LENGTHS(X) X(0, 16) X(1, 24) X(2, 32) X(3, 48) X(4, 64)
+#define MDFFT_SERVE_LINE_GROUP0(X) X(0, 16) X(1, 24) X(2, 32)
+#define MDFFT_SERVE_LINE_GROUP1(X) X(3, 48) X(4, 64)
 constexpr int kLineKind = 100;
 constexpr int kLineThreads = 128, kLineWarps = kLineThreads / 32;
+constexpr int line_group(int kind) { return kind - kLineKind >= 3 ? 1 : 0; }
 constexpr size_t kArgsBytes = (sizeof(PassArgs) + 15) / 16 * 16;
 constexpr size_t cmax2(size_t a, size_t b) { return a > b ? a : b; }
 #define MDFFT_LINE_RS_MAX(i, N) cmax2((size_t)LineCfg<N>::RS,
 #define MDFFT_LINE_CLOSE(i, N) )
-constexpr size_t kLineRs = MDFFT_SERVE_LINE_LENGTHS(MDFFT_LINE_RS_MAX) 0 MDFFT_SERVE_LINE_LENGTHS(MDFFT_LINE_CLOSE);
+// staging row stride of each group: its longest line's
+constexpr size_t kLineRs[2] = {MDFFT_SERVE_LINE_GROUP0(MDFFT_LINE_RS_MAX) 0 MDFFT_SERVE_LINE_GROUP0(MDFFT_LINE_CLOSE),
+                               MDFFT_SERVE_LINE_GROUP1(MDFFT_LINE_RS_MAX) 0 MDFFT_SERVE_LINE_GROUP1(MDFFT_LINE_CLOSE)};
 // per warp: the item's arguments, 32 staging rows, 32 line offsets
-constexpr size_t kLineWarpSmem = kArgsBytes + 32 * kLineRs * sizeof(float2) + 32 * sizeof(int64_t);
-constexpr size_t kLineSmem = kLineWarps * kLineWarpSmem;
+constexpr size_t line_warp_smem(int g) { return kArgsBytes + 32 * kLineRs[g] * sizeof(float2) + 32 * sizeof(int64_t); }
+constexpr size_t kLineSmem[2] = {kLineWarps * line_warp_smem(0), kLineWarps * line_warp_smem(1)};
 
 int line_kind_of(int64_t n) {
     switch (n) {
@@ -174,21 +184,23 @@ __global__ void __launch_bounds__(kThreads, 4) serve_kernel(const Table *tab) {
     }
 }
 
-// The line kernel: warp w of the grid takes chunks of chunk2 consecutive
-// 32-line tiles of the line items in turn; it copies an item's arguments to
-// its own shared memory when it reaches the item's tiles (items are in
-// increasing tile order, so lookups only advance).  No CTA barrier.
-__global__ void __launch_bounds__(kLineThreads, 2) serve_line_kernel(const Table *tab) {
+// A line kernel (group G): warp w of the grid takes chunks of
+// chunk_line[G] consecutive 32-line tiles of the group's items in turn; it
+// copies an item's arguments to its own shared memory when it reaches the
+// item's tiles (items are in increasing tile order, so lookups only
+// advance).  No CTA barrier.  Registers: group 0 fits 4 CTAs per SM, group 1 2.
+template <int G>
+__global__ void __launch_bounds__(kLineThreads, G == 0 ? 4 : 2) serve_line_kernel(const Table *tab) {
     extern __shared__ __align__(16) unsigned char line_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wsm = line_smem + warp * kLineWarpSmem;
+    unsigned char *wsm = line_smem + warp * line_warp_smem(G);
     PassArgs &args = *reinterpret_cast<PassArgs *>(wsm);
     float2 *stage = reinterpret_cast<float2 *>(wsm + kArgsBytes);
-    int64_t *lbase = reinterpret_cast<int64_t *>(stage + 32 * kLineRs);
-    const Item *items = tab->items + tab->n;
-    const int n = tab->n2;
-    const int64_t total = tab->total2;
-    const int64_t chunk = tab->chunk2;
+    int64_t *lbase = reinterpret_cast<int64_t *>(stage + 32 * kLineRs[G]);
+    const Item *items = tab->items + tab->n + (G == 1 ? tab->n_line[0] : 0);
+    const int n = tab->n_line[G];
+    const int64_t total = tab->total_line[G];
+    const int64_t chunk = tab->chunk_line[G];
     const int64_t gw = (int64_t)blockIdx.x * kLineWarps + warp, nw = (int64_t)gridDim.x * kLineWarps;
     int cur = -1, kind = -1;
     int64_t cur_start = 0, cur_end = 0;
@@ -212,16 +224,24 @@ __global__ void __launch_bounds__(kLineThreads, 2) serve_line_kernel(const Table
                 __syncwarp();
             }
             const TileCoord c = tile_coords(args, t - cur_start);
-            switch (kind) {
 #define MDFFT_RUN(i, N)                                           \
     case kLineKind + i:                                           \
         line_warp<N>(args, c, 0, stage, lbase, lane);             \
         break;
-                MDFFT_SERVE_LINE_LENGTHS(MDFFT_RUN)
-#undef MDFFT_RUN
-                default:
-                    break;
+            if constexpr (G == 0) {
+                switch (kind) {
+                    MDFFT_SERVE_LINE_GROUP0(MDFFT_RUN)
+                    default:
+                        break;
+                }
+            } else {
+                switch (kind) {
+                    MDFFT_SERVE_LINE_GROUP1(MDFFT_RUN)
+                    default:
+                        break;
+                }
             }
+#undef MDFFT_RUN
         }
 }
 
@@ -327,10 +347,10 @@ struct mdfft_server_s {
     int depth = 2;  // steps in flight on the GPU at most; arrivals in between join the next step
     int chunk = 4;  // at most this many consecutive tiles dealt to a CTA at a time
     int direct = 4;  // low load: at most this many requests with passes left run them as plain launches
-    int lines = 1;   // passes of 16 to 64 points go to the line kernel
-    int line_grid = 0;
-    cudaStream_t capture2 = nullptr;            // the line kernel's branch of the step graph
-    cudaEvent_t fork = nullptr, join = nullptr;  // the branch starts after the table copy, the step ends after both
+    int lines = 1;   // passes of 16 to 64 points go to the line kernels
+    int line_grid[2] = {0, 0};
+    cudaStream_t capture2[2] = {nullptr, nullptr};            // the line kernels' branches of the step graph
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};  // branches start after the table copy, the step ends after all
     Slot slots[kSlots];
     int next_slot = 0;
     cudaEvent_t t0 = nullptr;
@@ -349,11 +369,15 @@ mdfft_status capture_graphs(mdfft_server_t s) {
         // the two kernels are parallel branches: the line kernel's CTAs take
         // SMs as the grouped kernel's CTAs finish, and the other way round
         cudaEventRecord(s->fork, s->capture);
-        cudaStreamWaitEvent(s->capture2, s->fork, 0);
+        cudaStreamWaitEvent(s->capture2[0], s->fork, 0);
+        cudaStreamWaitEvent(s->capture2[1], s->fork, 0);
         serve_kernel<<<s->grid, kThreads, kSmem, s->capture>>>(sl.dev);
-        serve_line_kernel<<<s->line_grid, kLineThreads, kLineSmem, s->capture2>>>(sl.dev);
-        cudaEventRecord(s->join, s->capture2);
-        cudaStreamWaitEvent(s->capture, s->join, 0);
+        serve_line_kernel<0><<<s->line_grid[0], kLineThreads, kLineSmem[0], s->capture2[0]>>>(sl.dev);
+        serve_line_kernel<1><<<s->line_grid[1], kLineThreads, kLineSmem[1], s->capture2[1]>>>(sl.dev);
+        for (int g = 0; g < 2; ++g) {
+            cudaEventRecord(s->join[g], s->capture2[g]);
+            cudaStreamWaitEvent(s->capture, s->join[g], 0);
+        }
         e = cudaStreamEndCapture(s->capture, &sl.graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
@@ -471,10 +495,12 @@ mdfft_status mdfft_server_create(mdfft_server_t *out, size_t budget_bytes, int m
     if ((e = cudaMalloc(&s->arena_mem, s->arena_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc arena"));
     s->arena.reset(s->arena_bytes);
     if ((e = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&s->capture2, cudaStreamNonBlocking)) != cudaSuccess)
+        (e = cudaStreamCreateWithFlags(&s->capture2[0], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&s->capture2[1], cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaStreamCreate"));
     if ((e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&s->join[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->join[1], cudaEventDisableTiming)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaEventCreate"));
     if ((e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
         cudaSuccess)
@@ -484,12 +510,15 @@ mdfft_status mdfft_server_create(mdfft_server_t *out, size_t budget_bytes, int m
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kThreads, kSmem);
     s->grid = std::max(1, sms * std::max(1, per_sm));
-    if ((e = cudaFuncSetAttribute(serve_line_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmem)) !=
-        cudaSuccess)
-        return bail(cuda_fail(e, "cudaFuncSetAttribute"));
-    int line_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&line_per_sm, serve_line_kernel, kLineThreads, kLineSmem);
-    s->line_grid = std::max(1, sms * std::max(1, line_per_sm));
+    const void *line_fn[2] = {(const void *)serve_line_kernel<0>, (const void *)serve_line_kernel<1>};
+    for (int g = 0; g < 2; ++g) {
+        if ((e = cudaFuncSetAttribute(line_fn[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmem[g])) !=
+            cudaSuccess)
+            return bail(cuda_fail(e, "cudaFuncSetAttribute"));
+        int line_per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&line_per_sm, line_fn[g], kLineThreads, kLineSmem[g]);
+        s->line_grid[g] = std::max(1, sms * std::max(1, line_per_sm));
+    }
     for (Slot &sl : s->slots) {
         if ((e = cudaHostAlloc((void **)&sl.host, sizeof(Table), cudaHostAllocDefault)) != cudaSuccess)
             return bail(cuda_fail(e, "cudaHostAlloc table"));
@@ -601,26 +630,27 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
         return MDFFT_OK;
     }
     Table *tab = sl.host;
-    int n = 0, n2 = 0;
-    int64_t total = 0, total2 = 0;
+    int n = 0, n_line[2] = {0, 0};
+    int64_t total = 0, total_line[2] = {0, 0};
     std::vector<std::pair<Request *, PassArgs>> separate;  // lengths the persistent kernels do not carry
-    std::vector<Item> line_items;
+    std::vector<Item> line_items[2];
     for (Request *r : todo) {
-        if (n + n2 >= kMaxItems) break;
+        if (n + n_line[0] + n_line[1] >= kMaxItems) break;
         const int pass = r->next_pass;
         const PassArgs a = pass_args(s, r, pass);
         const ServePass &sp = s->retiled[r->plan][pass];
         const bool al16 = (uintptr_t)a.in % 16 == 0 && (uintptr_t)a.out % 16 == 0;
-        if (s->lines && sp.line_kind >= 0 && al16) {  // the same pass in 32-line tiles for the line kernel
-            line_items.emplace_back();
-            Item &it = line_items.back();
+        if (s->lines && sp.line_kind >= 0 && al16) {  // the same pass in 32-line tiles for a line kernel
+            const int g = line_group(sp.line_kind);
+            line_items[g].emplace_back();
+            Item &it = line_items[g].back();
             it.args = sp.line_args;
             it.args.in = a.in, it.args.out = a.out, it.args.tw = a.tw;
             it.args.conj = a.conj, it.args.scale = a.scale, it.args.scaled = a.scaled;
-            it.start = total2;
+            it.start = total_line[g];
             it.kind = sp.line_kind;
-            total2 += sp.line_tiles;
-            n2++;
+            total_line[g] += sp.line_tiles;
+            n_line[g]++;
         } else if (sp.kind < 0) {
             separate.push_back({r, a});
         } else {  // the same pass re-tiled for the persistent kernel's CTA
@@ -643,11 +673,14 @@ mdfft_status mdfft_server_step(mdfft_server_t s, int *launched) {
     // the step's tiles spread over every CTA first: chunks of total / grid tiles, at most s->chunk
     tab->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(s->chunk, total / std::max(1, s->grid)));
     tab->total = total;
-    for (int i = 0; i < n2; ++i) tab->items[n + i] = line_items[i];
-    tab->n2 = n2;
-    tab->chunk2 = (int)std::max<int64_t>(
-        1, std::min<int64_t>(s->chunk, total2 / std::max<int64_t>(1, (int64_t)s->line_grid * kLineWarps)));
-    tab->total2 = total2;
+    for (int g = 0, at = n; g < 2; ++g) {
+        for (int i = 0; i < n_line[g]; ++i) tab->items[at++] = line_items[g][i];
+        tab->n_line[g] = n_line[g];
+        tab->chunk_line[g] = (int)std::max<int64_t>(
+            1, std::min<int64_t>(s->chunk, total_line[g] / std::max<int64_t>(1, (int64_t)s->line_grid[g] * kLineWarps)));
+        tab->total_line[g] = total_line[g];
+    }
+    const int n2 = n_line[0] + n_line[1];
     if (n + n2 > 0) {
         if (sl.copy) {  // copy only the header and the items of this step
             const size_t used = offsetof(Table, items) + (size_t)(n + n2) * sizeof(Item);
@@ -832,9 +865,11 @@ mdfft_status mdfft_server_destroy(mdfft_server_t s) {
     }
     if (s->t0) cudaEventDestroy(s->t0);
     if (s->capture) cudaStreamDestroy(s->capture);
-    if (s->capture2) cudaStreamDestroy(s->capture2);
+    for (int g = 0; g < 2; ++g) {
+        if (s->capture2[g]) cudaStreamDestroy(s->capture2[g]);
+        if (s->join[g]) cudaEventDestroy(s->join[g]);
+    }
     if (s->fork) cudaEventDestroy(s->fork);
-    if (s->join) cudaEventDestroy(s->join);
     if (s->arena_mem) cudaFree(s->arena_mem);
     for (auto &kv : s->plans) mdfft_destroy(kv.second);
     for (auto &kv : s->requests) delete kv.second;
