@@ -68,25 +68,26 @@ template <int N, int RP = 0, int WARPS = 4> struct LineCfg {
 };
 
 // One warp's 32 lines of tile c: tile lines w0 .. w0 + 31, lane = line - w0.
-// stage: the warp's 32 staging rows (RS elements each), lbase: 32 entries.
-// Begins with __syncwarp, so a warp may run it for tile after tile.
+// line_issue copies them into the warp's 32 staging rows (RS elements each;
+// lbase: 32 entries) as one cp.async commit group; line_finish, once that
+// group has landed and the warp has met at __syncwarp, transforms and stores
+// them.  line_issue begins with __syncwarp, so a warp may refill rows it has
+// read before.
 template <int N, int RP = 0>
-__device__ __forceinline__ void line_warp(const PassArgs &a, const TileCoord &c, int w0, float2 *stage,
-                                          int64_t *lbase, int lane) {
+__device__ __forceinline__ void line_issue(const PassArgs &a, const TileCoord &c, int w0, float2 *stage,
+                                           int64_t *lbase, int lane) {
     using LC = LineCfg<N, RP, 1>;
     using C = float2;
     const C *in = reinterpret_cast<const C *>(a.in);
-    C *out = reinterpret_cast<C *>(a.out);
-    const C *gtw = reinterpret_cast<const C *>(a.tw);
     const int line = w0 + lane;
     int bg, bh;
     tile_line(a, line, bg, bh);
     const bool ok = line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
     const int64_t ib = c.in_base + (int64_t)bg * a.in_sg + (int64_t)bh * a.in_sh;
-    __syncwarp();  // the previous tile's reads of the rows and offsets are done
+    __syncwarp();  // earlier reads of these rows and offsets are done
     lbase[lane] = ok ? ib : -1;
     __syncwarp();
-    // the warp's 32 lines into its rows: unit e = lane + 32 i is unit u of line l
+    // unit e = lane + 32 i is unit u of line l
 #pragma unroll
     for (int i = 0; i < LC::CH; ++i) {
         const int e = lane + 32 * i, l = e / LC::CH, u = e - l * LC::CH;
@@ -97,9 +98,20 @@ __device__ __forceinline__ void line_warp(const PassArgs &a, const TileCoord &c,
         }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncwarp();
+}
 
+template <int N, int RP = 0>
+__device__ __forceinline__ void line_finish(const PassArgs &a, const TileCoord &c, int w0, const float2 *stage,
+                                            int lane) {
+    using LC = LineCfg<N, RP, 1>;
+    using C = float2;
+    C *out = reinterpret_cast<C *>(a.out);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+    const int line = w0 + lane;
+    int bg, bh;
+    tile_line(a, line, bg, bh);
+    const bool ok = line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
+    const int64_t ib = c.in_base + (int64_t)bg * a.in_sg + (int64_t)bh * a.in_sh;
     C x[N];
     const C *row = stage + lane * LC::RS;
 #pragma unroll
@@ -143,6 +155,16 @@ __device__ __forceinline__ void line_warp(const PassArgs &a, const TileCoord &c,
             if (split) atomicAdd(a.split, split);
         }
     }
+}
+
+// The whole tile for one warp: copy, wait, transform and store.
+template <int N, int RP = 0>
+__device__ __forceinline__ void line_warp(const PassArgs &a, const TileCoord &c, int w0, float2 *stage,
+                                          int64_t *lbase, int lane) {
+    line_issue<N, RP>(a, c, w0, stage, lbase, lane);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    line_finish<N, RP>(a, c, w0, stage, lane);
 }
 
 // One tile of LINES = 32 WARPS lines per CTA; warp w takes tile lines 32 w ..

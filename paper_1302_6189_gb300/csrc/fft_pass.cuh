@@ -241,10 +241,13 @@ template <typename Real, int N, int TC = 0, int THR = 0, int RP = 0> struct Pass
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
-// Sums of two products with the contraction written out: one rounded
-// product and one fused multiply-add, the same in every kernel that inlines
-// them (left to the compiler, either product may be the fused one, and
-// kernels that compute the same butterflies could round differently).
+// Every multiply-add of the butterflies is written out as one fused
+// multiply-add (fmadd) or, for a sum of two products, one rounded product
+// and one fused multiply-add (fma_prod): left to the compiler, whether and
+// which product is fused can differ between kernels that inline the same
+// butterflies (register pressure, scheduling), and their results with it.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }  // a b + c
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_prod(float a, float b, float c, float d) {
     return __fmaf_rn(a, b, __fmul_rn(c, d));  // a b + c d
 }
@@ -284,9 +287,9 @@ template <int K, typename C> __device__ __forceinline__ void butterfly16(C &lo, 
         constexpr double c = cos16(K), s = sin16(K);
         constexpr bool by_c = (c < 0 ? -c : c) >= (s < 0 ? -s : s);
         constexpr R f = (R)(by_c ? c : s), t = (R)(by_c ? s / c : c / s);
-        const C u = by_c ? C{o.x + t * o.y, o.y - t * o.x} : C{o.y + t * o.x, t * o.y - o.x};
-        lo = C{e.x + f * u.x, e.y + f * u.y};
-        hi = C{e.x - f * u.x, e.y - f * u.y};
+        const C u = by_c ? C{fmadd(t, o.y, o.x), fmadd(-t, o.x, o.y)} : C{fmadd(t, o.x, o.y), fmadd(t, o.y, -o.x)};
+        lo = C{fmadd(f, u.x, e.x), fmadd(f, u.y, e.y)};
+        hi = C{fmadd(-f, u.x, e.x), fmadd(-f, u.y, e.y)};
     }
 }
 
@@ -318,11 +321,11 @@ template <typename C> __device__ __forceinline__ void dft3(C (&v)[3]) {
     using R = decltype(v[0].x);
     const R s = (R)0.86602540378443864676;  // sin(2 pi / 3)
     C t1 = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-    C m = {v[0].x - (R)0.5 * t1.x, v[0].y - (R)0.5 * t1.y};
+    C m = {fmadd((R)-0.5, t1.x, v[0].x), fmadd((R)-0.5, t1.y, v[0].y)};
     v[0] = cadd(v[0], t1);
     // -i s d and +i s d
-    v[1] = {m.x + s * d.y, m.y - s * d.x};
-    v[2] = {m.x - s * d.y, m.y + s * d.x};
+    v[1] = {fmadd(s, d.y, m.x), fmadd(-s, d.x, m.y)};
+    v[2] = {fmadd(-s, d.y, m.x), fmadd(s, d.x, m.y)};
 }
 
 template <typename C> __device__ __forceinline__ void dft5(C (&v)[5]) {
@@ -332,8 +335,8 @@ template <typename C> __device__ __forceinline__ void dft5(C (&v)[5]) {
     C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
     C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
     C x0 = v[0];
-    C p1 = {x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y};
-    C p2 = {x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y};
+    C p1 = {fmadd(c2, a2.x, fmadd(c1, a1.x, x0.x)), fmadd(c2, a2.y, fmadd(c1, a1.y, x0.y))};
+    C p2 = {fmadd(c1, a2.x, fmadd(c2, a1.x, x0.x)), fmadd(c1, a2.y, fmadd(c2, a1.y, x0.y))};
     C q1 = {fma_prod(s1, b1.x, s2, b2.x), fma_prod(s1, b1.y, s2, b2.y)};    // X1 = p1 - i q1, X4 = p1 + i q1
     C q2 = {fma_prod(s2, b1.x, -s1, b2.x), fma_prod(s2, b1.y, -s1, b2.y)};  // X2 = p2 - i q2, X3 = p2 + i q2
     v[0] = {x0.x + a1.x + a2.x, x0.y + a1.y + a2.y};

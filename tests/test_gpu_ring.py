@@ -20,9 +20,10 @@ DEV = torch.device("cuda", 0)
 RING = [v for v in md.mdfft.TUNING_VARIANTS if v.startswith("ring") or v.startswith("line")]
 
 
-def ring_tuning(pl, variant, tile):
-    """The plan's tuning with `variant` and `tile` on every pass whose length has it."""
-    base = pl.tuning()
+def ring_tuning(pl, variant, tile, base=None):
+    """`base` (default: the plan's current tuning) with `variant` and `tile` on
+    every pass whose length has it; the plan is left at `base`."""
+    base = pl.tuning() if base is None else base
     chosen = [dict(d) for d in base]
     hit = []
     for s in range(len(base)):
@@ -49,10 +50,12 @@ def test_ring_variants_give_the_default_bits(shape, P, batch):
         want = pl.exec(x)
         want_inv = pl.exec(want, dir=1, normalize=True)
         want_counts = pl.exec_counted(x)[1].cpu().tolist()
+        default = pl.tuning()
         tried, walks = 0, 0.0
         for v in RING:
             for tile in ((8, 8), (5, 3), (16, 4), (24, 5)):
-                chosen, hit = ring_tuning(pl, v, tile)
+                # the variant on every pass it is built for, the default kernel elsewhere
+                chosen, hit = ring_tuning(pl, v, tile, default)
                 if not hit:
                     continue
                 ref = want
