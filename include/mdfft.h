@@ -366,7 +366,9 @@ mdfft_status mdfft_pass_describe(mdfft_plan_t plan, int s, mdfft_pass_info *out)
  * line with every radix stage in registers (lengths 8, 12, 16, 20, 24, 30,
  * 32, 40, 48, 60, 64; 16-byte aligned arrays; 128-line CTAs), 24 the same
  * with 64-line CTAs (48, 60, 64), 25 the same with the alternative radix
- * plan (32, 64);
+ * plan (32, 64), 26 / 27 two threads per line, the stages in registers and
+ * one exchange of values between them (32, 64; default / alternative radix
+ * plan);
  * lines per tile along g; lines per tile along h; tile order 0 or 1, see
  * mdfft_pass_info), e.g. after
  * mdfft_plan_autotune, to store and give back to a plan of the same dims, P,

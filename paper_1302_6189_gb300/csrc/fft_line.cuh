@@ -179,4 +179,141 @@ __global__ void __launch_bounds__(LineCfg<N, RP, WARPS>::THREADS) fft_pass_line_
     line_warp<N, RP>(a, c, w0, stage + w0 * LC::RS, lbase + w0, lane);
 }
 
+// Two threads per line, for two-stage plans whose radices are even (32 = 8 x 4,
+// 64 = 8 x 8, and the alternative plans 16 x 2, 16 x 4): half the registers
+// of one thread per line, so more warps per SM for the longer short lines.
+// Lane pair (2 l, 2 l + 1) owns line l of the warp's 16; lane parity t holds
+// the points of index parity t.  The first stage's butterflies j = 2 q + t
+// read only those points (their inputs j + r R1 have the parity of j, R1
+// even); the second stage's butterfly j1 = 2 p + t needs column j1 of every
+// first-stage row, half of them held by the partner lane, which sends them
+// in one exchange of N / 4 values (warp shuffle, lane ^ 1).  Same
+// butterflies, twiddles and order as Stages::simt: bit-identical results.
+template <int N, int RP = 0> struct Line2Cfg {
+    static constexpr RadixPlan plan = PassCfg<float, N, 0, 0, RP>::plan;
+    static constexpr int R0 = plan.R[0], R1 = plan.R[1], H = N / 2;
+    static_assert(plan.S == 2 && R0 % 2 == 0 && R1 % 2 == 0 && N % 4 == 0, "two stages, even radices");
+    static constexpr int WARPS = 4, LPW = 16, LINES = LPW * WARPS, THREADS = 32 * WARPS;
+    static constexpr int CH = N / 2;                   // 16-byte units per line
+    static constexpr int RS = N % 4 == 2 ? N : N + 2;  // row stride 2 mod 4: lanes (l, t) on distinct banks
+    static constexpr int TWOFF1 = tw_offset(plan, 1);
+    static constexpr size_t SMEM = (size_t)LINES * RS * sizeof(float2) + (size_t)LINES * sizeof(int64_t);
+};
+
+template <int N, int RP = 0>
+__device__ __forceinline__ void line2_warp(const PassArgs &a, const TileCoord &c, int w0, float2 *stage,
+                                           int64_t *lbase, int lane) {
+    using L2 = Line2Cfg<N, RP>;
+    using C = float2;
+    constexpr int R0 = L2::R0, R1 = L2::R1;
+    const C *in = reinterpret_cast<const C *>(a.in);
+    C *out = reinterpret_cast<C *>(a.out);
+    const C *gtw = reinterpret_cast<const C *>(a.tw);
+    const int l = lane >> 1, t = lane & 1, line = w0 + l;
+    int bg, bh;
+    tile_line(a, line, bg, bh);
+    const bool ok = line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
+    const int64_t ib = c.in_base + (int64_t)bg * a.in_sg + (int64_t)bh * a.in_sh;
+    if (t == 0) lbase[l] = ok ? ib : -1;
+    __syncwarp();
+    // the warp's 16 lines into its rows: unit e = lane + 32 i is unit u of line ll
+#pragma unroll
+    for (int i = 0; i < L2::CH / 2; ++i) {
+        const int e = lane + 32 * i, ll = e / L2::CH, u = e - ll * L2::CH;
+        const int64_t b = lbase[ll];
+        if (b >= 0) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(stage + ll * L2::RS + 2 * u);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(in + b + 2 * u) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+
+    C x[L2::H];  // points 2 m + t of the line
+    const C *row = stage + l * L2::RS + t;
+#pragma unroll
+    for (int m = 0; m < L2::H; ++m) x[m] = row[2 * m];
+    if (a.conj & 1)
+#pragma unroll
+        for (int m = 0; m < L2::H; ++m) x[m].y = -x[m].y;
+    // first stage (no twiddles): butterfly j = 2 q + t reads points j + r R1 = x[q + r R1 / 2]
+    C y[R1 / 2][R0];
+#pragma unroll
+    for (int q = 0; q < R1 / 2; ++q) {
+        C v[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[r] = x[q + r * (R1 / 2)];
+        dft<R0>(v);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) y[q][r] = v[r];
+    }
+    // exchange: send column 2 p + 1 - t of every own row, receive column 2 p + t of the partner's
+    C z[R1 / 2][R0 / 2];
+#pragma unroll
+    for (int q = 0; q < R1 / 2; ++q)
+#pragma unroll
+        for (int p = 0; p < R0 / 2; ++p) {
+            const C snd = t ? y[q][2 * p] : y[q][2 * p + 1];
+            z[q][p].x = __shfl_xor_sync(0xffffffffu, snd.x, 1);
+            z[q][p].y = __shfl_xor_sync(0xffffffffu, snd.y, 1);
+        }
+    // second stage: butterfly j1 = 2 p + t reads column j1 of rows r (row r of parity t is own)
+    const int64_t ob = c.out_base + (int64_t)bh * a.out_sh + (int64_t)bg * a.out_sg;
+    C *op = out + ob;
+    const bool plain = !(a.conj & 2) && !a.scaled;
+    const float sc = (float)a.scale, sy = (a.conj & 2) ? -sc : sc;
+#pragma unroll
+    for (int p = 0; p < R0 / 2; ++p) {
+        const int j1 = 2 * p + t;
+        C v[R1];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const C own = (r & 1) ? y[r / 2][2 * p + 1] : y[r / 2][2 * p];
+            v[r] = ((r & 1) == t) ? own : z[r / 2][p];
+        }
+#pragma unroll
+        for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], __ldg(gtw + L2::TWOFF1 + r * R0 + j1));
+        dft<R1>(v);
+        if (ok) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int64_t k = j1 + r * R0;
+                op[k * a.out_sf] = plain ? v[r] : C{v[r].x * sc, v[r].y * sy};
+            }
+        }
+    }
+    if (a.moved) {  // count mode: every point of the line once (each lane its parity), the split amount once
+        unsigned long long moved = 0, split = 0;
+        if (ok) {
+            for (int k = t; k < N; k += 2)
+                moved += owner_of(a.own_in, ib + k) != owner_of(a.own_out, ob + k * a.out_sf);
+            if (t == 0)
+                split = (unsigned long long)N *
+                        ((owner_of(a.own_in, ib + N - 1) - owner_of(a.own_in, ib)) / a.own_in.line_div);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            moved += __shfl_down_sync(0xffffffffu, moved, o);
+            split += __shfl_down_sync(0xffffffffu, split, o);
+        }
+        if (lane == 0) {
+            if (moved) atomicAdd(a.moved, moved);
+            if (split) atomicAdd(a.split, split);
+        }
+    }
+}
+
+// One tile of 64 lines per CTA; warp w takes tile lines 16 w ..
+template <int N, int RP = 0>
+__global__ void __launch_bounds__(Line2Cfg<N, RP>::THREADS) fft_pass_line2_kernel(const PassArgs a) {
+    using L2 = Line2Cfg<N, RP>;
+    extern __shared__ __align__(16) unsigned char line2_smem[];
+    float2 *stage = reinterpret_cast<float2 *>(line2_smem);                     // [LINES][RS]
+    int64_t *lbase = reinterpret_cast<int64_t *>(stage + L2::LINES * L2::RS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, w0 = warp * L2::LPW;
+    const TileCoord c = tile_coords(a, blockIdx.x);
+    line2_warp<N, RP>(a, c, w0, stage + w0 * L2::RS, lbase + w0, lane);
+}
+
 }  // namespace mdfft

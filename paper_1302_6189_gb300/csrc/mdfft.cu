@@ -1014,6 +1014,8 @@ mdfft_status mdfft_plan_autotune(mdfft_plan_t p, const void *in, void *out, int 
                 if (ring_variant(ps.n, rv, (p->flags & MDFFT_PLAN_TUNE_RADIX) != 0, &k) && al16) variants.push_back(k);
             for (int lv = 0; lv < kLineVariants; ++lv)
                 if (line_variant(ps.n, lv, (p->flags & MDFFT_PLAN_TUNE_RADIX) != 0, &k) && al16) variants.push_back(k);
+            for (int rp = 0; rp < ((p->flags & MDFFT_PLAN_TUNE_RADIX) ? 2 : 1); ++rp)
+                if (mdfft::find_pass_kernel_line2(ps.n, rp, &k) && al16) variants.push_back(k);
             if ((p->flags & MDFFT_PLAN_TUNE_RADIX) && mdfft::find_pass_kernel_c64_alt(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_occ(ps.n, &k)) variants.push_back(k);
             if (mdfft::find_pass_kernel_c64_shfl(ps.n, &k)) variants.push_back(k);
@@ -1114,14 +1116,18 @@ namespace {
 // SM), 14 / 15 the same with the alternative radix plan, 16 the 256-point
 // kernel with a warp-shuffle exchange between its two stages, 17-22 the
 // ring-of-slots kernel (kRing[variant - 17]: slots, CTAs per SM, radix plan),
-// 23-25 one thread per line with the stages in registers (kLine[variant - 23]).
+// 23-25 one thread per line with the stages in registers (kLine[variant - 23]),
+// 26 / 27 two threads per line (default / alternative radix plan).
 constexpr int kLineVariant = 17 + kRingVariants;
-constexpr int kTuningVariants = kLineVariant + kLineVariants;
+constexpr int kLine2Variant = kLineVariant + kLineVariants;
+constexpr int kTuningVariants = kLine2Variant + 2;
 bool tuning_kernel(const mdfft_plan_s *p, int s, int variant, PassKernel *k) {
     const int64_t n = p->pass[s].n;
     if (variant >= 17 && variant < kLineVariant) return p->dt == MDFFT_C64 && ring_variant(n, variant - 17, true, k);
-    if (variant >= kLineVariant && variant < kTuningVariants)
+    if (variant >= kLineVariant && variant < kLine2Variant)
         return p->dt == MDFFT_C64 && line_variant(n, variant - kLineVariant, true, k);
+    if (variant >= kLine2Variant && variant < kTuningVariants)
+        return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_line2(n, variant - kLine2Variant, k);
     switch (variant) {
         case 16:
             return p->dt == MDFFT_C64 && mdfft::find_pass_kernel_c64_shfl(n, k);

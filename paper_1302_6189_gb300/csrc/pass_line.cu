@@ -45,4 +45,20 @@ bool find_pass_kernel_line(int64_t n, int rp, int warps, PassKernel *k) {
     }
 }
 
+// Two threads per line (fft_pass_line2_kernel): 32 and 64, default or alternative radix plan.
+template <int N, int RP> static PassKernel make_line2() {
+    using L2 = Line2Cfg<N, RP>;
+    PassKernel k{(const void *)&fft_pass_line2_kernel<N, RP>, L2::THREADS, L2::LINES, 2, L2::SMEM, L2::plan};
+    k.bulk = 1;  // 16-byte copies from line starts: input and output 16-byte aligned
+    return k;
+}
+
+bool find_pass_kernel_line2(int64_t n, int rp, PassKernel *k) {
+    if (rp != 0 && rp != 1) return false;
+    if (n == 32) *k = rp ? make_line2<32, 1>() : make_line2<32, 0>();
+    else if (n == 64) *k = rp ? make_line2<64, 1>() : make_line2<64, 0>();
+    else return false;
+    return true;
+}
+
 }  // namespace mdfft

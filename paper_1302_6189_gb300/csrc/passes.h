@@ -56,6 +56,7 @@ bool find_pass_kernel_c64_pf(int64_t n, int rp, int minb, PassKernel *k);  // pe
 bool find_pass_kernel_c64_shfl(int64_t n, PassKernel *k);          // 256: warp-shuffle exchange between the stages
 bool find_pass_kernel_ring(int64_t n, int slots, int per_sm, int rp, PassKernel *k);  // persistent, ring of slots
 bool find_pass_kernel_line(int64_t n, int rp, int warps, PassKernel *k);  // one thread per line, stages in registers
+bool find_pass_kernel_line2(int64_t n, int rp, PassKernel *k);  // two threads per line (32, 64), one exchange
 bool find_move_kernel_c64(int64_t n, PassKernel *k);               // data movement of a pass, no FFT
 bool find_move_ring_kernel_c64(int64_t n, int slots, PassKernel *k);  // the same through a ring of slots
 

@@ -201,7 +201,7 @@ def mdfft_selftest_wait(arrive, limit_us):
 
 TUNING_VARIANTS = ("default", "thr256", "thr512", "pipe1", "pipe2", "tc128", "thr192", "thr384", "radix_alt", "occ6", "tcg", "tcg_direct", "pf2", "pf4",
                    "pf2_radix_alt", "pf4_radix_alt", "shfl256", "ring2x3", "ring3x2", "ring2x4", "ring2x2",
-                   "ring2x3_radix_alt", "ring3x2_radix_alt", "line", "line2w", "line_radix_alt")
+                   "ring2x3_radix_alt", "ring3x2_radix_alt", "line", "line2w", "line_radix_alt", "line2t", "line2t_radix_alt")
 
 
 def mdfft_plan_tuning(plan, M):
