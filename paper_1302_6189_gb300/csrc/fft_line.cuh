@@ -214,6 +214,7 @@ __device__ __forceinline__ void line2_warp(const PassArgs &a, const TileCoord &c
     tile_line(a, line, bg, bh);
     const bool ok = line < a.Bg * a.Bh && c.g0 + bg < a.Ng && c.h0 + bh < a.Nh;
     const int64_t ib = c.in_base + (int64_t)bg * a.in_sg + (int64_t)bh * a.in_sh;
+    __syncwarp();  // earlier reads of these rows and offsets are done (a warp may run tile after tile)
     if (t == 0) lbase[l] = ok ? ib : -1;
     __syncwarp();
     // the warp's 16 lines into its rows: unit e = lane + 32 i is unit u of line ll
