@@ -105,17 +105,19 @@ def test_ring_24_cubed_four_dims_against_the_oracle():
     assert err < 1e-5, err
 
 
-@pytest.mark.parametrize("shape,P", [((24, 24, 24, 24), 64), ((16, 48, 32, 8), 16), ((64, 60, 40), 8)])
-def test_line_kernel_on_every_pass_against_the_oracle(shape, P):
-    # every pass whose length has the one-thread-per-line kernel runs it, with
-    # the default tiles; element-wise against the FP64 oracle, forward and
-    # normalised inverse
+@pytest.mark.parametrize("shape,P,variant", [((24, 24, 24, 24), 64, "line"), ((16, 48, 32, 8), 16, "line"),
+                                             ((64, 60, 40), 8, "line"), ((64, 64, 32, 8), 64, "line2t"),
+                                             ((32, 64, 20), 16, "line2t_radix_alt")])
+def test_line_kernel_on_every_pass_against_the_oracle(shape, P, variant):
+    # every pass whose length has the one-thread-per-line (or two-threads-per-
+    # line) kernel runs it, with the default tiles; element-wise against the
+    # FP64 oracle, forward and normalised inverse
     x = si.uniform_complex(shape, 996, np.complex64)
     with md.Plan(shape, P, None, "c64") as pl:
         base = pl.tuning()
-        chosen, hit = ring_tuning(pl, "line", (base[0]["tile_g"], base[0]["tile_h"]))
+        chosen, hit = ring_tuning(pl, variant, (base[0]["tile_g"], base[0]["tile_h"]))
         if not hit:
-            chosen, hit = ring_tuning(pl, "line", (8, 4))
+            chosen, hit = ring_tuning(pl, variant, (8, 4))
         assert hit
         pl.set_tuning(chosen)
         xd = torch.from_numpy(x).to(DEV)
