@@ -829,12 +829,10 @@ def md_study(dev, reps=10):
                              "pattern_bound_gbs": [round(2 * B * T * 8 / (v * 1e-3) / 1e9, 1) for v in pattern_ms],
                              "movement_bound_gbs": [round(2 * B * T * 8 / (v * 1e-3) / 1e9, 1) if v else None
                                                     for v in movement_ms],
-                             # the probes move data the way the default kernel (pattern) or the ring
-                             # kernel (movement) does, with the pass's tiles where they fit those
-                             # kernels' CTAs, else the default tiling: for the passes on the one- or
-                             # two-threads-per-line kernels they are no bound
-                             "probe_structure": ["default tiling" if t["variant"].startswith("line") else "pass tiles"
-                                                 for t in tuning],
+                             "probe_note": "the probes move a pass's data the way the default kernel (pattern) "
+                                           "or the ring kernel (movement) does, with the pass's tiles where they "
+                                           "fit that kernel's CTA, else its default tiling; they bound those "
+                                           "kernels, not the one- or two-threads-per-line ones",
                              "roofline": pass_roofline(2 * B * T * 8, pass_ms, MD_PROFILES.get(name))}
     return out
 
